@@ -1,0 +1,150 @@
+// Kernel argument blocks and host launchers of the sixdgs library.
+#pragma once
+
+#include "common.cuh"
+
+namespace sixdgs {
+
+struct ProjectArgs {
+  const CamRec* cams;
+  int32_t n_cams;
+  int64_t n;
+  int32_t sh_degree;
+  float lambda_opa;
+  float inv_tile_w, inv_tile_h;
+  const float* mu_p;
+  const float* mu_d;
+  const float* l_raw;
+  const float* opacity_logit;
+  const float* sh;
+  PairRec* rec;
+  uint32_t* ntiles;
+  ushort4* rect;
+  uint32_t* depth_key;
+  float* grad_rec;   // zeroed for every visible pair (read by the backward)
+  int32_t* status;
+};
+
+// Visible-pair compaction (scan of ntiles > 0) feeding the depth sort.
+struct CompactArgs {
+  const uint32_t* ntiles;
+  const uint32_t* depth_key;
+  int64_t n_pairs;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  uint32_t* n_vis_out;
+  unsigned long long* scan_state;  // one word per scan tile
+  uint32_t* tile_counter;
+  uint32_t* hist;                  // passes x 256
+  int32_t passes;
+  int64_t spin_budget;
+  int32_t* status;
+};
+
+struct OnesweepArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  const uint32_t* n_ptr;   // element count (device)
+  uint32_t capacity;       // buffer size; counts above it are clamped
+  const uint32_t* hist;    // 256 digit counts of this pass
+  uint32_t* lookback;      // tiles x 256 status words of this pass
+  uint32_t* tile_counter;
+  int32_t shift;
+  int64_t spin_budget;
+  int32_t* status;
+};
+
+// Duplicate emission in depth order (scan of ntiles over the depth-sorted
+// visible pairs) feeding the tile sort.
+struct EmitArgs {
+  const uint32_t* pairs;      // depth-sorted visible pair indices
+  const uint32_t* n_vis;
+  const uint32_t* ntiles;
+  const ushort4* rect;
+  const CamRec* cams;
+  int64_t n;                  // Gaussians per camera
+  uint32_t n_pairs;
+  uint32_t* keys_out;         // global tile id
+  uint32_t* vals_out;         // pair index
+  uint64_t capacity;
+  uint32_t* k_out;            // number of duplicates (may exceed capacity)
+  unsigned long long* scan_state;
+  uint32_t* tile_counter;
+  uint32_t* hist;
+  int32_t passes;
+  int64_t spin_budget;
+  int32_t* status;
+};
+
+struct RangesArgs {
+  const uint32_t* keys;
+  const uint32_t* k_ptr;
+  uint32_t capacity;
+  uint32_t total_tiles;
+  uint2* ranges;
+};
+
+struct BlendArgs {
+  const CamRec* cams;
+  int32_t n_cams;
+  int32_t tile_w, tile_h, batch;
+  const PairRec* rec;
+  uint32_t n_pairs;
+  const uint32_t* sorted;   // pair index per list entry
+  const uint2* ranges;
+  float bg[3];
+  float* images;
+  const float* targets;
+  float* grad_images;
+  double* loss;
+  float inv_count;          // 1 / (3 * total_pixels)
+  uint32_t* nwalk;          // optional per-pixel walk length
+  // backward
+  const float* images_in;
+  const float* grad_in;
+  float* grad_rec;          // n_pairs x 12
+  int32_t recompute;        // 1: re-derive the stop; 0: use nwalk
+};
+
+struct ProjectBwdArgs {
+  const CamRec* cams;
+  int32_t n_cams;
+  int64_t n;
+  int32_t sh_degree;
+  float lambda_opa;
+  const float* mu_p;
+  const float* mu_d;
+  const float* l_raw;
+  const float* opacity_logit;
+  const float* sh;
+  const PairRec* rec;
+  const uint32_t* ntiles;
+  const float* grad_rec;
+  float* grad_mu_p;
+  float* grad_mu_d;
+  float* grad_l_raw;
+  float* grad_opacity_logit;
+  float* grad_sh;
+};
+
+void launch_project_fwd(const ProjectArgs& a, cudaStream_t stream);
+void launch_compact(const CompactArgs& a, int grid, cudaStream_t stream);
+void launch_onesweep(const OnesweepArgs& a, int grid, cudaStream_t stream);
+void launch_emit(const EmitArgs& a, int grid, cudaStream_t stream);
+void launch_ranges(const RangesArgs& a, int grid, cudaStream_t stream);
+void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
+void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
+void launch_sh_bwd(const ProjectBwdArgs& a, cudaStream_t stream);
+void launch_geom_bwd(const ProjectBwdArgs& a, cudaStream_t stream);
+
+// Tile geometry of the scans and sorts (elements per block tile).
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+}  // namespace sixdgs

@@ -1,0 +1,376 @@
+// Stage 2: binning and sorting of (view, Gaussian) pairs into per-tile lists
+// ordered by depth (the 3DGS duplicate/sort step kept by 6DGS section 4.4).
+//
+// The composite key (global tile, depth, Gaussian id) is sorted LSD-first:
+//   1. compact_kernel   -- visible pairs in (view, id) order, with the depth
+//                          digits' histograms (single-pass scan, decoupled
+//                          look-back);
+//   2. onesweep passes  -- stable 8-bit digit passes over the depth key;
+//   3. emit_kernel      -- duplicate each pair once per touched tile, in depth
+//                          order, with the tile digits' histograms;
+//   4. onesweep passes  -- stable passes over the global tile id;
+//   5. ranges_kernel    -- [start, end) of every tile's list.
+// Because every pass is stable and the depth passes run before duplication,
+// the result equals one LSD sort of the full key while the depth passes
+// touch each visible pair once instead of once per tile.
+//
+// The per-digit passes follow the single-pass "onesweep" design (Adinets and
+// Merrill, 2022): a tile's digit counts are published with decoupled
+// look-back (Merrill and Garland, 2016) so each pass reads and writes the
+// data once.  Every spin is bounded by a clock budget; on expiry the kernel
+// reports SIXDGS_ERR_TIMEOUT and carries on with in-bounds writes only.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sixdgs {
+
+constexpr unsigned long long kScanAgg = 1ull << 62;
+constexpr unsigned long long kScanInc = 2ull << 62;
+constexpr unsigned long long kScanValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void st_volatile64(unsigned long long* p, unsigned long long v) {
+  *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// Exclusive block scan of one value per thread; returns the thread's prefix
+// and the block total through `total`.  s_warp needs THREADS/32 + 1 words.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
+  constexpr int WARPS = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < WARPS ? s_warp[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < WARPS) s_warp[lane] = wi - w;
+    if (lane == WARPS - 1) s_warp[WARPS] = wi;
+  }
+  __syncthreads();
+  total = s_warp[WARPS];
+  uint32_t r = s_warp[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+// Decoupled look-back over 64-bit scan state, run by one full warp.
+// Publishes this tile's aggregate, waits for the predecessors and
+// publishes the inclusive prefix.  Returns the exclusive prefix.
+__device__ unsigned long long scan_lookback(unsigned long long* state, uint32_t tile,
+                                            unsigned long long block_total, int64_t budget,
+                                            int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_volatile64(&state[0], kScanInc | block_total);
+    return 0;
+  }
+  if (lane == 0) st_volatile64(&state[tile], kScanAgg | block_total);
+  unsigned long long excl = 0;
+  long long p = (long long)tile - 1;
+  const long long t0 = clock64();
+  bool timed_out = false;
+  while (true) {
+    long long idx = p - lane;
+    unsigned long long w = idx >= 0 ? ld_volatile64(&state[idx]) : kScanInc;
+    uint32_t flag = (uint32_t)(w >> 62);
+    uint32_t inc = __ballot_sync(0xffffffffu, flag == 2u);
+    uint32_t not_ready = __ballot_sync(0xffffffffu, flag == 0u);
+    int i_inc = inc ? __ffs(inc) - 1 : 32;
+    uint32_t need = i_inc >= 31 ? 0xffffffffu : ((2u << i_inc) - 1u);
+    if (not_ready & need) {
+      bool expired = __shfl_sync(0xffffffffu, (clock64() - t0) > budget, 0);
+      if (expired) {
+        timed_out = true;
+        break;
+      }
+      continue;
+    }
+    unsigned long long val = (lane <= i_inc) ? (w & kScanValMask) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+    excl += val;
+    if (i_inc < 32) break;
+    p -= 32;
+  }
+  if (lane == 0) {
+    if (timed_out) raise_status(status, SIXDGS_ERR_TIMEOUT);
+    st_volatile64(&state[tile], kScanInc | ((excl + block_total) & kScanValMask));
+  }
+  return excl;
+}
+
+// --------------------------------------------------------------------------
+// 1. Visible-pair compaction + depth-digit histograms
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) compact_kernel(CompactArgs a) {
+  __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+  __shared__ uint32_t s_hist[4 * 256];
+  __shared__ uint32_t s_tile;
+  __shared__ unsigned long long s_excl;
+  for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
+  const uint64_t n = (uint64_t)a.n_pairs;
+  const uint32_t num_tiles = (uint32_t)((n + kScanTile - 1) / kScanTile);
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= num_tiles) break;
+    const uint64_t base = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t cnt[kScanItems];
+    if (base + kScanItems <= n) {
+      uint4 q = *reinterpret_cast<const uint4*>(a.ntiles + base);
+      cnt[0] = q.x; cnt[1] = q.y; cnt[2] = q.z; cnt[3] = q.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanItems; ++k) cnt[k] = (base + k < n) ? a.ntiles[base + k] : 0u;
+    }
+    uint32_t vis = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) vis += cnt[k] > 0u;
+    uint32_t total;
+    uint32_t excl = block_excl_scan<kScanThreads>(vis, total, s_warp);
+    if (threadIdx.x < 32) {
+      unsigned long long e = scan_lookback(a.scan_state, tile, total, a.spin_budget, a.status);
+      if (threadIdx.x == 0) s_excl = e;
+    }
+    __syncthreads();
+    uint64_t off = s_excl + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (cnt[k] > 0u) {
+        uint32_t key = a.depth_key[base + k];
+        if (off < n) {
+          a.keys_out[off] = key;
+          a.vals_out[off] = (uint32_t)(base + k);
+        }
+        ++off;
+        for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
+      }
+    }
+    if (tile == num_tiles - 1 && threadIdx.x == 0) *a.n_vis_out = (uint32_t)(s_excl + total);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.passes * 256; i += kScanThreads)
+    if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+}
+
+// --------------------------------------------------------------------------
+// 2/4. One stable 8-bit digit pass (onesweep)
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(OnesweepArgs a) {
+  constexpr int WARPS = kSortThreads / 32;
+  static_assert(kSortThreads == 256, "one thread per digit");
+  __shared__ uint32_t s_whist[WARPS][256];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_dstart[256];
+  __shared__ uint32_t s_glob[256];
+  __shared__ uint32_t s_warp[WARPS + 1];
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t n = min(*a.n_ptr, a.capacity);
+  const uint32_t num_tiles = (n + kSortTile - 1) / kSortTile;
+  // exclusive digit offsets of the whole pass (thread tid owns digit tid)
+  uint32_t htot;
+  const uint32_t hist_excl = block_excl_scan<kSortThreads>(a.hist[tid], htot, s_warp);
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  while (true) {
+    __syncthreads();
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) s_whist[w][tid] = 0u;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= num_tiles) break;
+    const uint32_t base = tile * kSortTile;
+    const uint32_t wbase = base + warp * (32 * kSortItems);
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      uint32_t idx = wbase + j * 32 + lane;
+      bool valid = idx < n;
+      key[j] = valid ? a.keys_in[idx] : 0xffffffffu;
+      val[j] = valid ? a.vals_in[idx] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      uint32_t idx = wbase + j * 32 + lane;
+      uint32_t d = idx < n ? (key[j] >> a.shift) & 255u : 256u;
+      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
+      __syncwarp();
+      if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) s_whist[warp][d] = before + __popc(peers);
+      __syncwarp();
+      rank[j] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, block count
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = run;
+      run += c;
+    }
+    const uint32_t cnt = run;
+    uint32_t btot;
+    const uint32_t dstart = block_excl_scan<kSortThreads>(cnt, btot, s_warp);
+    s_dstart[tid] = dstart;
+    // decoupled look-back for digit tid
+    uint32_t* lb = a.lookback;
+    uint32_t excl = 0;
+    if (tile == 0) {
+      st_volatile(&lb[tid], kFlagInc | cnt);
+    } else {
+      st_volatile(&lb[tile * 256 + tid], kFlagAgg | cnt);
+      long long p = (long long)tile - 1;
+      const long long t0 = clock64();
+      while (p >= 0) {
+        uint32_t w = ld_volatile(&lb[p * 256 + tid]);
+        uint32_t f = w & kFlagMask;
+        if (f == 0u) {
+          if (clock64() - t0 > a.spin_budget) {
+            raise_status(a.status, SIXDGS_ERR_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        excl += w & kValMask;
+        if (f == kFlagInc) break;
+        --p;
+      }
+      st_volatile(&lb[tile * 256 + tid], kFlagInc | ((excl + cnt) & kValMask));
+    }
+    s_glob[tid] = hist_excl + excl - dstart;
+    __syncthreads();
+    // local scatter into digit order
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      uint32_t idx = wbase + j * 32 + lane;
+      if (idx < n) {
+        uint32_t d = (key[j] >> a.shift) & 255u;
+        uint32_t pos = s_dstart[d] + s_whist[warp][d] + rank[j];
+        s_keys[pos] = key[j];
+        s_vals[pos] = val[j];
+      }
+    }
+    __syncthreads();
+    const uint32_t tile_n = min((uint32_t)kSortTile, n - base);
+    for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+      uint32_t k = s_keys[i];
+      uint32_t out = s_glob[(k >> a.shift) & 255u] + i;
+      if (out < n) {
+        a.keys_out[out] = k;
+        a.vals_out[out] = s_vals[i];
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// 3. Duplicate emission in depth order + tile-digit histograms
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) emit_kernel(EmitArgs a) {
+  __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+  __shared__ uint32_t s_hist[4 * 256];
+  __shared__ uint32_t s_tile;
+  __shared__ unsigned long long s_excl;
+  for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
+  const uint32_t n_vis = *a.n_vis;
+  const uint32_t num_tiles = (n_vis + kScanTile - 1) / kScanTile;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= num_tiles) break;
+    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
+    uint32_t pair[kScanItems], cnt[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      bool valid = base + k < n_vis;
+      pair[k] = valid ? a.pairs[base + k] : 0u;
+      valid = valid && pair[k] < a.n_pairs;
+      cnt[k] = valid ? a.ntiles[pair[k]] : 0u;
+      sum += cnt[k];
+    }
+    uint32_t total;
+    uint32_t excl = block_excl_scan<kScanThreads>(sum, total, s_warp);
+    if (threadIdx.x < 32) {
+      unsigned long long e = scan_lookback(a.scan_state, tile, total, a.spin_budget, a.status);
+      if (threadIdx.x == 0) s_excl = e;
+    }
+    __syncthreads();
+    uint64_t off = s_excl + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (cnt[k] == 0u) continue;
+      const uint32_t p = pair[k];
+      const CamRec& cam = a.cams[p / (uint32_t)a.n];
+      const ushort4 r = a.rect[p];
+      for (uint32_t ty = r.z; ty < r.w; ++ty) {
+        for (uint32_t tx = r.x; tx < r.y; ++tx) {
+          const uint32_t key = (uint32_t)cam.tile_offset + ty * (uint32_t)cam.tiles_x + tx;
+          if (off < a.capacity) {
+            a.keys_out[off] = key;
+            a.vals_out[off] = p;
+            for (int q = 0; q < a.passes; ++q) atomicAdd(&s_hist[q * 256 + ((key >> (8 * q)) & 255u)], 1u);
+          }
+          ++off;
+        }
+      }
+    }
+    if (tile == num_tiles - 1 && threadIdx.x == 0) {
+      unsigned long long k_total = s_excl + total;
+      *a.k_out = (uint32_t)min(k_total, 0xffffffffull);
+      if (k_total > a.capacity) raise_status(a.status, SIXDGS_ERR_CAPACITY);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.passes * 256; i += kScanThreads)
+    if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+}
+
+// --------------------------------------------------------------------------
+// 5. Per-tile ranges in the sorted duplicate list
+// --------------------------------------------------------------------------
+__global__ void ranges_kernel(RangesArgs a) {
+  const uint32_t k = min(*a.k_ptr, a.capacity);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const uint32_t t = a.keys[i];
+    if (t >= a.total_tiles) continue;
+    if (i == 0 || a.keys[i - 1] != t) a.ranges[t].x = i;
+    if (i == k - 1 || a.keys[i + 1] != t) a.ranges[t].y = i + 1;
+  }
+}
+
+void launch_compact(const CompactArgs& a, int grid, cudaStream_t stream) {
+  compact_kernel<<<grid, kScanThreads, 0, stream>>>(a);
+}
+void launch_onesweep(const OnesweepArgs& a, int grid, cudaStream_t stream) {
+  onesweep_kernel<<<grid, kSortThreads, 0, stream>>>(a);
+}
+void launch_emit(const EmitArgs& a, int grid, cudaStream_t stream) {
+  emit_kernel<<<grid, kScanThreads, 0, stream>>>(a);
+}
+void launch_ranges(const RangesArgs& a, int grid, cudaStream_t stream) {
+  ranges_kernel<<<grid, 256, 0, stream>>>(a);
+}
+
+}  // namespace sixdgs

@@ -1,0 +1,262 @@
+"""PyTorch-facing wrapper of the sixdgs C ABI.
+
+PyTorch only provides device memory and streams here: every stage of the
+render runs in the CUDA kernels of libsixdgs.so.  There is no CPU path; the
+renderer refuses to run without a CUDA device and the library.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+PARAM_NAMES = ("mu_p", "mu_d", "l_raw", "opacity_logit", "sh")
+
+
+def _camera_struct(cam) -> _lib.Camera:
+    c = _lib.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    w2c = np.asarray(cam.world_to_cam, dtype=np.float64).reshape(3, 4)
+    for i in range(12):
+        c.world_to_cam[i] = float(w2c.reshape(-1)[i])
+    for i in range(3):
+        c.campos[i] = float(np.asarray(cam.campos, dtype=np.float64)[i])
+    c.znear = float(getattr(cam, "znear", 0.2))
+    return c
+
+
+def camera_array(cams):
+    arr = (_lib.Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = _camera_struct(c)
+    return arr
+
+
+def make_settings(tile=(16, 16), batch=256, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
+                  spin_budget=0) -> _lib.Settings:
+    s = _lib.Settings()
+    s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
+    s.batch = int(batch)
+    s.lambda_opa = float(lambda_opa)
+    for i in range(3):
+        s.bg[i] = float(bg[i])
+    s.store_aux = 1 if store_aux else 0
+    s.spin_budget = int(spin_budget)
+    return s
+
+
+def make_plan(n, sh_degree, cams, settings, dup_capacity=0) -> _lib.Plan:
+    lib = _lib.load()
+    plan = _lib.Plan()
+    arr = camera_array(cams)
+    _lib.check(lib.sixdgs_plan_init(int(n), int(sh_degree), arr, len(cams), ctypes.byref(settings),
+                                    int(dup_capacity), ctypes.byref(plan)), "sixdgs_plan_init")
+    return plan
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def params_to_device(scene, device="cuda"):
+    """Scene planes (synth.Scene or dict of arrays) as contiguous float32 device tensors."""
+    planes = scene.planes() if hasattr(scene, "planes") else scene
+    return {k: torch.as_tensor(np.asarray(planes[k], dtype=np.float32)).to(device).contiguous()
+            for k in PARAM_NAMES}
+
+
+class Renderer:
+    """Plan + workspace of one frame shape (scene size, cameras, settings).
+
+    One frame may be in flight per renderer: forward() followed by at most
+    one backward() on the same stream.
+    """
+
+    def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=256, lambda_opa=0.35,
+                 bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, device="cuda"):
+        if not torch.cuda.is_available():
+            raise _lib.SixDGSError("sixdgs needs a CUDA device; there is no CPU path")
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        self.n, self.sh_degree = int(n), int(sh_degree)
+        self.cameras = list(cameras)
+        self.settings = make_settings(tile, batch, lambda_opa, bg, store_aux, spin_budget)
+        self.cams = camera_array(self.cameras)
+        self._make_plan(dup_capacity)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.sizes = [(int(c.height), int(c.width)) for c in self.cameras]
+
+    def _make_plan(self, dup_capacity):
+        self.plan = make_plan(self.n, self.sh_degree, self.cameras, self.settings, dup_capacity)
+        self.ws = torch.empty(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
+
+    # ---- structs --------------------------------------------------------
+    def scene_struct(self, params) -> _lib.Scene:
+        s = _lib.Scene()
+        s.n, s.sh_degree = self.n, self.sh_degree
+        for k in PARAM_NAMES:
+            t = params[k]
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), k
+            setattr(s, k, t.data_ptr())
+        return s
+
+    def _stream(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _wsargs(self):
+        return ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws.numel())
+
+    @property
+    def total_pixels(self) -> int:
+        return int(self.plan.total_pixels)
+
+    def new_images(self):
+        return torch.empty(3 * self.total_pixels, dtype=torch.float32, device=self.device)
+
+    def split(self, flat):
+        """Per-camera (3, H, W) views of a packed image buffer."""
+        out, o = [], 0
+        for (h, w) in self.sizes:
+            out.append(flat[o:o + 3 * h * w].view(3, h, w))
+            o += 3 * h * w
+        return out
+
+    def pack(self, images):
+        return torch.cat([torch.as_tensor(i, dtype=torch.float32).reshape(-1) for i in images]).to(self.device)
+
+    # ---- stages -----------------------------------------------------------
+    def condition_project(self, params, stream=None):
+        ws, nb = self._wsargs()
+        sc = self.scene_struct(params)
+        _lib.check(self.lib.sixdgs_condition_project(ctypes.byref(self.plan), ctypes.byref(sc), self.cams,
+                                                     ws, nb, _ptr(self.status), self._stream(stream)),
+                   "sixdgs_condition_project")
+
+    def bin_sort(self, stream=None):
+        ws, nb = self._wsargs()
+        _lib.check(self.lib.sixdgs_bin_sort(ctypes.byref(self.plan), ws, nb, _ptr(self.status),
+                                            self._stream(stream)), "sixdgs_bin_sort")
+
+    def raster_fwd(self, images, targets=None, grad_images=None, loss=None, stream=None):
+        ws, nb = self._wsargs()
+        _lib.check(self.lib.sixdgs_raster_fwd(ctypes.byref(self.plan), ws, nb, _ptr(images), _ptr(targets),
+                                              _ptr(grad_images), _ptr(loss), _ptr(self.status),
+                                              self._stream(stream)), "sixdgs_raster_fwd")
+
+    def raster_bwd(self, params, images, grad_images, grads, stream=None):
+        ws, nb = self._wsargs()
+        sc = self.scene_struct(params)
+        _lib.check(self.lib.sixdgs_raster_bwd(ctypes.byref(self.plan), ctypes.byref(sc), ws, nb,
+                                              _ptr(images), _ptr(grad_images), _ptr(grads["mu_p"]),
+                                              _ptr(grads["mu_d"]), _ptr(grads["l_raw"]),
+                                              _ptr(grads["opacity_logit"]), _ptr(grads["sh"]),
+                                              _ptr(self.status), self._stream(stream)), "sixdgs_raster_bwd")
+
+    def new_grads(self, params):
+        return {k: torch.empty_like(params[k]) for k in PARAM_NAMES}
+
+    # ---- frames -----------------------------------------------------------
+    def forward(self, params, targets=None, stream=None, check=True):
+        """Render every camera; returns the packed image buffer (and, with
+        targets, the L1 gradient image and loss)."""
+        for attempt in range(3):
+            self.status.zero_()
+            images = self.new_images()
+            gi = loss = None
+            if targets is not None:
+                gi = torch.empty_like(images)
+                self.loss.zero_()
+                loss = self.loss
+            self.condition_project(params, stream)
+            self.bin_sort(stream)
+            self.raster_fwd(images, targets, gi, loss, stream)
+            if not check:
+                break
+            st = int(self.status.item())
+            if st & (1 << _lib.ERR_CAPACITY):
+                k = int(self.counts()[1])
+                self._make_plan(int(k * 1.25) + 4096)
+                continue
+            self.raise_status(st)
+            break
+        if targets is not None:
+            return images, gi, loss
+        return images
+
+    def backward(self, params, images, grad_images, stream=None, grads=None):
+        grads = grads if grads is not None else self.new_grads(params)
+        self.raster_bwd(params, images, grad_images, grads, stream)
+        return grads
+
+    def raise_status(self, st=None):
+        st = int(self.status.item()) if st is None else st
+        if st:
+            raise _lib.SixDGSError("device status: " + ", ".join(_lib.status_names(st)))
+
+    # ---- workspace inspection (tests, diagnostics) ----------------------
+    def _section(self, idx, dtype, count):
+        off = int(self.plan.off[idx])
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nbytes].view(dtype)
+
+    def counts(self):
+        return self._section(_lib.WS_COUNTS, torch.int32, 4).cpu().numpy().astype(np.int64)
+
+    def records(self):
+        return self._section(_lib.WS_REC, torch.float32, 12 * int(self.plan.n_pairs)).view(-1, 12)
+
+    def ntiles(self):
+        return self._section(_lib.WS_NTILES, torch.int32, int(self.plan.n_pairs))
+
+    def rects(self):
+        return self._section(_lib.WS_RECT, torch.int16, 4 * int(self.plan.n_pairs)).view(-1, 4)
+
+    def sorted_pairs(self):
+        k = int(self.counts()[1])
+        return self._section(_lib.WS_SORTED, torch.int32, int(self.plan.dup_capacity))[:k]
+
+    def ranges(self):
+        return self._section(_lib.WS_RANGES, torch.int32, 2 * int(self.plan.total_tiles)).view(-1, 2)
+
+    def grad_records(self):
+        return self._section(_lib.WS_GRADREC, torch.float32, 12 * int(self.plan.n_pairs)).view(-1, 12)
+
+    def tile_offsets(self):
+        offs, o = [], 0
+        tw, th = self.settings.tile_w, self.settings.tile_h
+        for (h, w) in self.sizes:
+            offs.append(o)
+            o += ((w + tw - 1) // tw) * ((h + th - 1) // th)
+        return offs
+
+
+class RenderFunction(torch.autograd.Function):
+    """images = render(params); backward through the hand-written kernels."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, mu_p, mu_d, l_raw, opacity_logit, sh):
+        params = {"mu_p": mu_p.contiguous(), "mu_d": mu_d.contiguous(), "l_raw": l_raw.contiguous(),
+                  "opacity_logit": opacity_logit.contiguous(), "sh": sh.contiguous()}
+        images = renderer.forward(params)
+        ctx.renderer = renderer
+        ctx.params = params
+        ctx.save_for_backward(images)
+        return images
+
+    @staticmethod
+    def backward(ctx, grad_images):
+        (images,) = ctx.saved_tensors
+        g = ctx.renderer.backward(ctx.params, images, grad_images.contiguous())
+        return None, g["mu_p"], g["mu_d"], g["l_raw"], g["opacity_logit"], g["sh"]
+
+
+def render(renderer: Renderer, params):
+    """Differentiable render: packed images of every camera."""
+    return RenderFunction.apply(renderer, *(params[k] for k in PARAM_NAMES))
