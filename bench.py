@@ -1,0 +1,503 @@
+#!/usr/bin/env python3
+"""Throughput of the differentiable 6D Gaussian render on GB300.
+
+Workload (the headline configuration): 300,000 6D Gaussians on a noisy unit
+shell with strong position-direction coupling, a ring of 8 cameras at
+800x800, L1 loss against targets rendered from a seed-perturbed copy of the
+scene.  One step = condition_project + bin_sort + raster_fwd (fused L1) +
+raster_bwd for all 8 views, i.e. the whole hot path forward and backward.
+
+Arms:
+  ours (default)     batched: the 8 views in one launch sequence, replayed
+                     as one CUDA graph; also timed: the plain form (the same
+                     kernels launched once per view, no graph) and the
+                     end-to-end form (host parameters and targets copied in,
+                     gradients and loss copied out, every step).
+  --impl reference   the FP64 CPU oracle on a bounded sample of the same
+                     workload (CPU host cores).
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) execute
+independent replicas of the workload, one per GPU ("replicas only": the path
+has no exchange step within a step), and report the aggregate.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "fwd+bwd views/s @800², 300k 6D Gaussians: batched vs plain, same error bound"
+UNIT = "views/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 operations per (pixel, list entry) pair of the blend
+# (FMA = 2): every evaluated pair computes dx, dy and q (10); a compositing
+# pair adds min, 1-alpha, T(1-alpha), w and three colour FMAs (10) in the
+# forward, and in the backward the prefix (6), suffix (3), colour grads (3),
+# dL/dalpha (15), dq (2), the six geometry grads (12) and the 9-value sum
+# over pixels (9) -- 50 -- plus the same 10 + 10 as the forward replay.
+FLOPS_EVAL = 10
+FLOPS_COMP_FWD = 10
+FLOPS_COMP_BWD = 60
+MUFU_PER_COMP_FWD = 1
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=2, help="workload index (2 = headline)")
+    ap.add_argument("--n", type=int, default=0, help="override the Gaussian count (smaller runs)")
+    ap.add_argument("--tile", type=int, nargs=2, default=(16, 16))
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--store-aux", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run this many batched steps eagerly and exit (for ncu)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing
+# --------------------------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=2)
+
+    def summary(self, busy_mhz_floor=300.0):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        busy = [r for r in rows if r[0] >= busy_mhz_floor] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in busy for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def build_inputs(args):
+    w = synth.make_workload(args.config, n_override=args.n or None)
+    target_scene = synth.perturb(w.scene, synth.target_seed(args.config))
+    return w, target_scene
+
+
+def run_ours(args, world, rank, local):
+    import paper_2410_04974_gb300 as sx
+
+    dev = torch.device("cuda", local)
+    w, tscene = build_inputs(args)
+    cams = w.cameras
+    V = len(cams)
+    kw = dict(tile=tuple(args.tile), batch=args.batch, lambda_opa=w.lambda_opa, bg=w.bg, store_aux=args.store_aux)
+    # targets: render the perturbed scene once (untimed)
+    rt = sx.Renderer(tscene.n, tscene.sh_degree, cams, **kw)
+    targets = rt.forward(sx.params_to_device(tscene, dev))
+    torch.cuda.synchronize()
+    del rt
+
+    params = sx.params_to_device(w.scene, dev)
+    r = sx.Renderer(w.scene.n, w.scene.sh_degree, cams, **kw)
+    images = r.forward(params)                       # sizes the duplicate capacity
+    torch.cuda.synchronize()
+    cap = r.plan.dup_capacity
+    gimg = torch.empty_like(images)
+    grads = r.new_grads(params)
+
+    def step(rr=r, out_grads=grads):
+        rr.status.zero_()
+        rr.loss.zero_()
+        rr.condition_project(params)
+        rr.bin_sort()
+        rr.raster_fwd(images, targets, gimg, rr.loss)
+        rr.raster_bwd(params, images, gimg, out_grads)
+
+    step()
+    torch.cuda.synchronize()
+    r.raise_status()
+    counts = r.counts()
+
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            step()
+        torch.cuda.synchronize()
+        r.raise_status()
+        if rank == 0:
+            print(json.dumps({"profile_steps": args.profile_steps, "counts": counts.tolist()}))
+        return
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # ---- batched: one CUDA graph per step ----
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    r.raise_status()
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+        barrier(world)
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_id = vis.split(",")[local].strip() if vis else str(local)
+    with ClockSampler(smi_id) as clocks:
+        t_batched = timed(graph.replay, args.steps)
+    r.raise_status()
+    ms_batched = max_over_ranks(sum(t_batched) / len(t_batched), world)
+    img_batched = images.clone()
+    grads_batched = {k: v.clone() for k, v in grads.items()}
+    loss_batched = float(r.loss.item())
+
+    # ---- per-stage breakdown (eager launches, same flush discipline) ----
+    stage_names = ["condition_project", "bin_sort", "raster_fwd", "blend_bwd", "project_bwd"]
+
+    def staged():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        r.status.zero_()
+        r.loss.zero_()
+        ev[0].record()
+        r.condition_project(params)
+        ev[1].record()
+        r.bin_sort()
+        ev[2].record()
+        r.raster_fwd(images, targets, gimg, r.loss)
+        ev[3].record()
+        r.blend_bwd(images, gimg)
+        ev[4].record()
+        r.project_bwd(params, grads)
+        ev[5].record()
+        return ev
+
+    stage_steps = max(5, min(args.steps, 50))
+    all_ev = []
+    for _ in range(3):
+        staged()
+    torch.cuda.synchronize()
+    for _ in range(stage_steps):
+        flush.zero_()
+        all_ev.append(staged())
+    torch.cuda.synchronize()
+    stages = {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in all_ev) / stage_steps
+              for i, name in enumerate(stage_names)}
+
+    # ---- plain: same kernels, one camera at a time, no graph ----
+    plain = None
+    equiv = None
+    if not args.no_plain:
+        rp = sx.Renderer(w.scene.n, w.scene.sh_degree, [cams[0]], loss_norm=3.0 * r.total_pixels, **kw)
+        per_view = [slice(3 * sum(h * wd for (h, wd) in r.sizes[:v]), 3 * sum(h * wd for (h, wd) in r.sizes[:v + 1]))
+                    for v in range(V)]
+        grads_p = rp.new_grads(params)
+
+        def plain_step():
+            rp.status.zero_()
+            rp.loss.zero_()
+            for v in range(V):
+                rp.set_cameras([cams[v]])
+                sl = per_view[v]
+                rp.condition_project(params)
+                rp.bin_sort()
+                rp.raster_fwd(images[sl], targets[sl], gimg[sl], rp.loss)
+                rp.raster_bwd(params, images[sl], gimg[sl], grads_p, accumulate=v > 0)
+
+        for _ in range(max(3, args.warmup // 2)):
+            plain_step()
+        torch.cuda.synchronize()
+        rp.raise_status()
+        t_plain = timed(plain_step, max(10, args.steps // 4))
+        rp.raise_status()
+        ms_plain = max_over_ranks(sum(t_plain) / len(t_plain), world)
+        plain = {"value": V * 1000.0 / ms_plain * world, "unit": UNIT, "ms_per_step": ms_plain,
+                 "launches_per_step": V * 16, "graph": False}
+        g_rel = {k: float((grads_p[k] - grads_batched[k]).norm() / grads_batched[k].norm().clamp_min(1e-30))
+                 for k in grads_p}
+        equiv = {"image_max_abs": float((images - img_batched).abs().max()),
+                 "loss_abs": abs(float(rp.loss.item()) - loss_batched),
+                 "grad_rel_l2_max": max(g_rel.values())}
+        del rp
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.detach().cpu().pin_memory() for k, v in params.items()}
+        host_t = targets.cpu().pin_memory()
+        host_g = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in grads.items()}
+        host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host.values()) + host_t.numel() * 4
+        d2h = sum(v.numel() * 4 for v in host_g.values()) + 8
+
+        def e2e_step():
+            for k in params:
+                params[k].copy_(host[k], non_blocking=True)
+            targets.copy_(host_t, non_blocking=True)
+            step()
+            for k in grads:
+                host_g[k].copy_(grads[k], non_blocking=True)
+            host_loss.copy_(r.loss, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = timed(e2e_step, max(10, args.steps // 4))
+        ms_e2e = max_over_ranks(sum(t_e2e) / len(t_e2e), world)
+        e2e = {"value": V * 1000.0 / ms_e2e * world, "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel ----
+    rc = sx.Renderer(w.scene.n, w.scene.sh_degree, cams, count_pairs=True, **kw)
+    rc.forward(params)
+    torch.cuda.synchronize()
+    n_eval, n_comp = [int(x) for x in rc.pair_counts()]
+    del rc
+    clk = clocks.summary()
+    dom = max(("raster_fwd", "blend_bwd"), key=lambda s: stages[s])
+    dom_ms = stages[dom]
+    flops = n_eval * FLOPS_EVAL + n_comp * (FLOPS_COMP_FWD if dom == "raster_fwd" else FLOPS_COMP_BWD)
+    peak_clock = float(clk["sm_mhz"] or 2070.0)
+    peak = SMS * FP32_LANES_PER_SM * 2 * peak_clock * 1e6 / 1e12
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    kernel = {"raster_fwd": "blend_fwd_kernel", "blend_bwd": "blend_bwd_kernel"}[dom]
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_basis": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                              f"{peak_clock:.0f} MHz (median SM clock under load)",
+                "pairs_evaluated": n_eval, "pairs_compositing": n_comp, "kernel_ms": round(dom_ms, 4)}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(w, samples=1)
+
+    value = V * 1000.0 / ms_batched * world
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_batched, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n_gaussians": w.scene.n, "views": V,
+                   "resolution": f"{cams[0].width}x{cams[0].height}", "tile": list(args.tile),
+                   "batch": args.batch, "store_aux": bool(args.store_aux), "sh_degree": w.scene.sh_degree,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                   "graph": True, "visible_pairs": int(counts[0]), "duplicates": int(counts[1]),
+                   "dup_capacity": int(cap)},
+        "plain": plain, "speedup_vs_plain": round(plain["ms_per_step"] / ms_batched, 3) if plain else None,
+        "batched_vs_plain": equiv, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "gpu_launches": 16 * args.steps,
+        "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "loss": loss_batched,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# the oracle (CPU baseline and reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_baseline(w, samples=1, sample_tiles=8, seed=0):
+    """Views/s of the FP64 oracle, extrapolated from a bounded sample.
+
+    One sample = for one camera of the workload: the full per-Gaussian slice,
+    colour and projection of every Gaussian (no grad), plus forward and
+    backward (autograd) of `sample_tiles` tiles; the per-tile cost is scaled
+    to the camera's tiles with a non-empty list."""
+    from oracle import sixdgs_oracle as O
+
+    st = O.Settings(tile_w=16, tile_h=16, lambda_opa=w.lambda_opa, bg=w.bg)
+    rng = np.random.default_rng(seed)
+    per_view = []
+    total = 0.0
+    for s in range(samples):
+        cam = w.cameras[s % len(w.cameras)]
+        t0 = time.perf_counter()
+        with torch.no_grad():
+            prep = O.prepare_view(O.to_params(w.scene), w.scene.sh_degree, cam, st)
+        t_prep = time.perf_counter() - t0
+        tx, ty = O.tile_grid(cam, st)
+        rect = prep.rect.numpy()[prep.valid.numpy()]
+        occupied = np.zeros((ty, tx), bool)
+        for x0, x1, y0, y1 in rect:
+            occupied[y0:y1, x0:x1] = True
+        occ = np.argwhere(occupied)
+        pick = occ[rng.choice(len(occ), size=min(sample_tiles, len(occ)), replace=False)]
+        tiles = [(int(x), int(y)) for y, x in pick]
+        g = np.zeros((3, cam.height, cam.width), np.float32)
+        for (x, y) in tiles:
+            g[:, y * 16:(y + 1) * 16, x * 16:(x + 1) * 16] = rng.normal(size=(3, 16, 16))
+        t1 = time.perf_counter()
+        O.gradients(w.scene, [cam], [g], st, tiles=[tiles])
+        t_grad = time.perf_counter() - t1
+        # gradients() repeats the no-grad preparation once; the rest is per tile
+        t_tile = max(t_grad - t_prep, 0.0) / len(tiles)
+        per_view.append(t_prep + t_tile * len(occ))
+        total += t_prep + t_grad
+    view_s = float(np.mean(per_view))
+    return {"value": round(1.0 / view_s, 6), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{samples} view(s) of {w.name}: per-Gaussian slice/projection of all {w.scene.n} "
+                      f"Gaussians + fwd/bwd of {sample_tiles} occupied 16x16 tiles, scaled to the view's "
+                      f"occupied tiles ({float(np.mean([len(occ)])):.0f})",
+            "seconds_measured": round(total, 2)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w, _ = build_inputs(args)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle_baseline(w, samples=1, seed=k)
+        dt = 1.0 / r["value"]
+        if k >= args.warmup:
+            times.append(dt)
+    view_s = float(np.mean(times))
+    value = 1.0 / view_s
+    cpu = {"value": round(value, 6), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+           "sample": r["sample"]}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(view_s * 1000.0 * len(w.cameras), 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_gaussians": w.scene.n, "views": len(w.cameras),
+                       "resolution": f"{w.cameras[0].width}x{w.cameras[0].height}", "tile": [16, 16]},
+            "cpu_baseline": cpu, "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py (ours) needs a CUDA GPU")
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

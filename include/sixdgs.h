@@ -58,8 +58,8 @@ typedef enum sixdgs_status {
   SIXDGS_ERR_INVALID_ARG = 1, /* bad size, null pointer, unsupported setting  */
   SIXDGS_ERR_CUDA = 2,        /* a CUDA launch or copy failed                 */
   SIXDGS_ERR_CAPACITY = 3,    /* more (Gaussian, tile) duplicates than the
-                                 plan's dup_capacity: dup_count holds the
-                                 required number; grow and re-run             */
+                                 plan's dup_capacity: SIXDGS_WS_COUNTS[1]
+                                 holds the required number; grow, re-run      */
   SIXDGS_ERR_TIMEOUT = 4,     /* a device-side wait ran out of its budget     */
   SIXDGS_ERR_NONFINITE = 5,   /* a Gaussian produced a non-finite value; it
                                  was culled                                   */
@@ -116,6 +116,12 @@ typedef struct sixdgs_settings {
   int64_t spin_budget; /* clock cycles a device-side wait may spin before it
                           reports SIXDGS_ERR_TIMEOUT; <= 0 selects the default
                           (2^31 cycles, about one second)                     */
+  float loss_norm;     /* number of values the fused L1 mean divides by; <= 0
+                          selects 3 * total_pixels of the plan (use the whole
+                          batch's count when one batch is rendered one camera
+                          per plan)                                           */
+  int32_t count_pairs; /* 1: raster_fwd also counts evaluated and compositing
+                          (pixel, list entry) pairs into SIXDGS_WS_COUNTS     */
 } sixdgs_settings;
 
 /* Sizes and workspace layout of one frame, filled by sixdgs_plan_init. */
@@ -143,7 +149,9 @@ enum {
   SIXDGS_WS_NTILES = 2,    /* n_pairs x uint32 tiles touched (0 = culled)      */
   SIXDGS_WS_RECT = 3,      /* n_pairs x 4 uint16 tile rect x0, x1, y0, y1      */
   SIXDGS_WS_DEPTHKEY = 4,  /* n_pairs x uint32                                 */
-  SIXDGS_WS_COUNTS = 5,    /* uint32[4]: visible pairs, duplicates (K), -, -  */
+  SIXDGS_WS_COUNTS = 5,    /* uint32 visible pairs, uint32 duplicates (K),
+                              8 bytes unused, uint64 evaluated and uint64
+                              compositing (pixel, entry) pairs (count_pairs) */
   SIXDGS_WS_SORTED = 6,    /* dup_capacity x uint32 pair index, sorted by
                               (global tile, depth, Gaussian id)               */
   SIXDGS_WS_RANGES = 7,    /* total_tiles x uint32[2] [start, end) in SORTED  */
@@ -217,18 +225,39 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* plan, void* ws_dev, size_t ws
  * raw scene parameter, through the blend (replayed in sorted order, front
  * to back, with the suffix colour taken from the forward image), the
  * projection, the SH colour, the slice and the Cholesky activation.
+ * Equivalent to sixdgs_blend_bwd followed by sixdgs_project_bwd.
  * images_dev: the forward output; grad_images_dev: dL/dC, same layout.
- * grad_*: outputs with the layout of the scene planes; overwritten (the
- * sum over all cameras of the call).  The per-pair gradient records that
- * this call accumulates are zeroed by condition_project, so call
- * raster_bwd at most once per condition_project.
+ * grad_*: outputs with the layout of the scene planes; overwritten with the
+ * sum over all cameras of the plan, or added to when accumulate != 0.
+ * The per-pair gradient records that this call accumulates are zeroed by
+ * condition_project, so call it at most once per condition_project.
  * Errors: INVALID_ARG, WORKSPACE, CUDA. */
 sixdgs_status sixdgs_raster_bwd(const sixdgs_plan* plan, const sixdgs_scene* scene,
                                 void* ws_dev, size_t ws_bytes,
                                 const float* images_dev, const float* grad_images_dev,
                                 float* grad_mu_p, float* grad_mu_d, float* grad_l_raw,
-                                float* grad_opacity_logit, float* grad_sh,
+                                float* grad_opacity_logit, float* grad_sh, int32_t accumulate,
                                 int32_t* status_dev, sixdgs_stream_t stream);
+
+/* Stage 4a -- blend backward only (section 4.4, the differentiable 3DGS
+ * rasteriser): for every (view, Gaussian) pair, the gradient of
+ * sum <grad_images, images> with respect to the pair's screen record
+ * (2D mean, conic, alpha_cond, colour) is accumulated into the workspace
+ * section SIXDGS_WS_GRADREC.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* plan, void* ws_dev, size_t ws_bytes,
+                               const float* images_dev, const float* grad_images_dev,
+                               int32_t* status_dev, sixdgs_stream_t stream);
+
+/* Stage 4b -- per-Gaussian backward of the projection, SH colour (section
+ * 4.2), slice (Eq. mu, Eq. pdfv2, Eq. alpha), Schur complement (Eq. sigma)
+ * and Cholesky activation (section 3.1), summed over the plan's cameras, from
+ * the records that sixdgs_blend_bwd left.  grad_* as in sixdgs_raster_bwd.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA. */
+sixdgs_status sixdgs_project_bwd(const sixdgs_plan* plan, const sixdgs_scene* scene,
+                                 void* ws_dev, size_t ws_bytes, float* grad_mu_p,
+                                 float* grad_mu_d, float* grad_l_raw, float* grad_opacity_logit,
+                                 float* grad_sh, int32_t accumulate, int32_t* status_dev,
+                                 sixdgs_stream_t stream);
 
 #ifdef __cplusplus
 }

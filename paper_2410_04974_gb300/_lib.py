@@ -29,7 +29,8 @@ class Scene(ctypes.Structure):
 
 class Settings(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("lambda_opa", c_float),
-                ("bg", c_float * 3), ("store_aux", c_int32), ("spin_budget", c_int64)]
+                ("bg", c_float * 3), ("store_aux", c_int32), ("spin_budget", c_int64),
+                ("loss_norm", c_float), ("count_pairs", c_int32)]
 
 
 class Plan(ctypes.Structure):
@@ -52,7 +53,12 @@ EXPORTS = {
                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "sixdgs_raster_bwd": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), c_void_p, c_size_t,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                    c_void_p, c_void_p, c_void_p]),
+                                    c_void_p, c_int32, c_void_p, c_void_p]),
+    "sixdgs_blend_bwd": (c_int32, [ctypes.POINTER(Plan), c_void_p, c_size_t, c_void_p, c_void_p,
+                                   c_void_p, c_void_p]),
+    "sixdgs_project_bwd": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), c_void_p, c_size_t,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                     c_void_p, c_void_p]),
 }
 
 _LIB = None

@@ -183,7 +183,7 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   take(SIXDGS_WS_NWALK, st->store_aux ? pixels * 4 : 0);
   // cleared at the start of every bin_sort
   plan->off[WS_ZERO] = o;
-  take(SIXDGS_WS_COUNTS, 16);
+  take(SIXDGS_WS_COUNTS, 32);
   take(WS_COUNTERS, 64 * 4);
   take(WS_SCAN_C, scan_tiles * 8);
   take(WS_SCAN_E, scan_tiles * 8);
@@ -381,8 +381,13 @@ static BlendArgs blend_args(const sixdgs_plan* p, void* ws) {
   a.sorted = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_SORTED);
   a.ranges = ws_ptr<uint2>(ws, p, SIXDGS_WS_RANGES);
   for (int i = 0; i < 3; ++i) a.bg[i] = p->settings.bg[i];
-  a.inv_count = 1.f / (3.f * (float)p->total_pixels);
+  const double norm = p->settings.loss_norm > 0.f ? (double)p->settings.loss_norm
+                                                   : 3.0 * (double)p->total_pixels;
+  a.inv_count = (float)(1.0 / norm);
   a.nwalk = p->settings.store_aux ? ws_ptr<uint32_t>(ws, p, SIXDGS_WS_NWALK) : nullptr;
+  a.pair_counts = p->settings.count_pairs
+                      ? reinterpret_cast<unsigned long long*>(ws_ptr<char>(ws, p, SIXDGS_WS_COUNTS) + 16)
+                      : nullptr;
   return a;
 }
 
@@ -405,26 +410,34 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* p, void* ws, size_t ws_bytes,
   return launch_status();
 }
 
-sixdgs_status sixdgs_raster_bwd(const sixdgs_plan* p, const sixdgs_scene* scene, void* ws,
-                                size_t ws_bytes, const float* images_dev,
-                                const float* grad_images_dev, float* grad_mu_p, float* grad_mu_d,
-                                float* grad_l_raw, float* grad_opacity_logit, float* grad_sh,
-                                int32_t* status_dev, sixdgs_stream_t stream_) {
+sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, const float* images_dev,
+                               const float* grad_images_dev, int32_t* status_dev, sixdgs_stream_t stream_) {
   (void)status_dev;
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
-  if (!valid_scene(p, scene) || !images_dev || !grad_images_dev) return SIXDGS_ERR_INVALID_ARG;
-  if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
-    return SIXDGS_ERR_INVALID_ARG;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!images_dev || !grad_images_dev) return SIXDGS_ERR_INVALID_ARG;
   BlendArgs a = blend_args(p, ws);
   a.images_in = images_dev;
   a.grad_in = grad_images_dev;
   a.grad_rec = ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
   a.recompute = p->settings.store_aux ? 0 : 1;
-  launch_blend_bwd(a, p->total_tiles, stream);
+  launch_blend_bwd(a, p->total_tiles, reinterpret_cast<cudaStream_t>(stream_));
+  return launch_status();
+}
+
+sixdgs_status sixdgs_project_bwd(const sixdgs_plan* p, const sixdgs_scene* scene, void* ws,
+                                 size_t ws_bytes, float* grad_mu_p, float* grad_mu_d, float* grad_l_raw,
+                                 float* grad_opacity_logit, float* grad_sh, int32_t accumulate,
+                                 int32_t* status_dev, sixdgs_stream_t stream_) {
+  (void)status_dev;
+  sixdgs_status e = check_ws(p, ws, ws_bytes);
+  if (e != SIXDGS_OK) return e;
+  if (!valid_scene(p, scene)) return SIXDGS_ERR_INVALID_ARG;
+  if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
+    return SIXDGS_ERR_INVALID_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   ProjectBwdArgs b;
-  b.cams = a.cams;
+  b.cams = ws_ptr<CamRec>(ws, p, SIXDGS_WS_CAMS);
   b.n_cams = p->n_cams;
   b.n = p->n;
   b.sh_degree = p->sh_degree;
@@ -434,17 +447,34 @@ sixdgs_status sixdgs_raster_bwd(const sixdgs_plan* p, const sixdgs_scene* scene,
   b.l_raw = scene->l_raw;
   b.opacity_logit = scene->opacity_logit;
   b.sh = scene->sh;
-  b.rec = a.rec;
+  b.rec = ws_ptr<PairRec>(ws, p, SIXDGS_WS_REC);
   b.ntiles = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_NTILES);
-  b.grad_rec = a.grad_rec;
+  b.grad_rec = ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
   b.grad_mu_p = grad_mu_p;
   b.grad_mu_d = grad_mu_d;
   b.grad_l_raw = grad_l_raw;
   b.grad_opacity_logit = grad_opacity_logit;
   b.grad_sh = grad_sh;
+  b.accumulate = accumulate;
   launch_sh_bwd(b, stream);
   launch_geom_bwd(b, stream);
   return launch_status();
+}
+
+sixdgs_status sixdgs_raster_bwd(const sixdgs_plan* p, const sixdgs_scene* scene, void* ws,
+                                size_t ws_bytes, const float* images_dev,
+                                const float* grad_images_dev, float* grad_mu_p, float* grad_mu_d,
+                                float* grad_l_raw, float* grad_opacity_logit, float* grad_sh,
+                                int32_t accumulate, int32_t* status_dev, sixdgs_stream_t stream) {
+  sixdgs_status e = check_ws(p, ws, ws_bytes);
+  if (e != SIXDGS_OK) return e;
+  if (!valid_scene(p, scene)) return SIXDGS_ERR_INVALID_ARG;
+  if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
+    return SIXDGS_ERR_INVALID_ARG;
+  e = sixdgs_blend_bwd(p, ws, ws_bytes, images_dev, grad_images_dev, status_dev, stream);
+  if (e != SIXDGS_OK) return e;
+  return sixdgs_project_bwd(p, scene, ws, ws_bytes, grad_mu_p, grad_mu_d, grad_l_raw, grad_opacity_logit,
+                            grad_sh, accumulate, status_dev, stream);
 }
 
 }  // extern "C"

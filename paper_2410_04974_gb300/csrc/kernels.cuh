@@ -101,6 +101,7 @@ struct BlendArgs {
   double* loss;
   float inv_count;          // 1 / (3 * total_pixels)
   uint32_t* nwalk;          // optional per-pixel walk length
+  unsigned long long* pair_counts;  // optional: evaluated, compositing pairs
   // backward
   const float* images_in;
   const float* grad_in;
@@ -127,6 +128,7 @@ struct ProjectBwdArgs {
   float* grad_l_raw;
   float* grad_opacity_logit;
   float* grad_sh;
+  int32_t accumulate;   // 1: add into the outputs instead of overwriting
 };
 
 void launch_project_fwd(const ProjectArgs& a, cudaStream_t stream);

@@ -82,13 +82,20 @@ __global__ void __launch_bounds__(128) sh_bwd_kernel(ProjectBwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) dmp[i] += (gd[i] - d[i] * dot) * inv_len;
   }
+  const bool acc = a.accumulate != 0;
 #pragma unroll
   for (int k = 0; k < kMaxShCoeffs; ++k)
     if (k < K)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) a.grad_sh[(k * 3 + c) * n + g] = dbeta[k][c];
+      for (int c = 0; c < 3; ++c) {
+        float* o = a.grad_sh + (k * 3 + c) * n + g;
+        *o = acc ? *o + dbeta[k][c] : dbeta[k][c];
+      }
 #pragma unroll
-  for (int i = 0; i < 3; ++i) a.grad_mu_p[i * n + g] = dmp[i];
+  for (int i = 0; i < 3; ++i) {
+    float* o = a.grad_mu_p + i * n + g;
+    *o = acc ? *o + dmp[i] : dmp[i];
+  }
 }
 
 __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
@@ -274,21 +281,29 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
       for (int j = 0; j < 6; ++j) dL[i][j] = 0.f;
     galpha = 0.f;
   }
+  const bool acc = a.accumulate != 0;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) a.grad_l_raw[i * n + g] = dL[i][i] * L[i][i];
+  for (int i = 0; i < 6; ++i) {
+    float* o = a.grad_l_raw + i * n + g;
+    const float v = dL[i][i] * L[i][i];
+    *o = acc ? *o + v : v;
+  }
   int k = 6;
 #pragma unroll
   for (int i = 1; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < i; ++j) {
       const float v = L[i][j];
-      a.grad_l_raw[(k++) * n + g] = dL[i][j] * 0.5f * (1.f - v * v);
+      float* o = a.grad_l_raw + (k++) * n + g;
+      const float gv = dL[i][j] * 0.5f * (1.f - v * v);
+      *o = acc ? *o + gv : gv;
     }
-  a.grad_opacity_logit[g] = galpha * alpha * (1.f - alpha);
+  const float gl = galpha * alpha * (1.f - alpha);
+  a.grad_opacity_logit[g] = acc ? a.grad_opacity_logit[g] + gl : gl;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    a.grad_mu_d[i * n + g] = gmd[i];
-    a.grad_mu_p[i * n + g] += gmp[i];
+    a.grad_mu_d[i * n + g] = acc ? a.grad_mu_d[i * n + g] + gmd[i] : gmd[i];
+    a.grad_mu_p[i * n + g] += gmp[i];   // sh_bwd_kernel wrote (or added) its part first
   }
 }
 

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   bool done = !inside;
   uint32_t walked = range.y - range.x;
+  uint32_t n_eval = 0, n_comp = 0;
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
         const float4 ra = s_a[j], rb = s_b[j];
         float dx, dy;
         const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
+        ++n_eval;
         if (q < kQMin) continue;
         const float alpha = fminf(kAlphaMax, ex2_approx(q));
         const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
           walked = start - range.x + j;
           break;
         }
+        ++n_comp;
         const float w = __fmul_rn(alpha, T);
         C0 = __fmaf_rn(rb.z, w, C0);
         C1 = __fmaf_rn(rb.w, w, C1);
@@ -110,6 +113,18 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
         gi[ch * hw + pix] = diff > 0.f ? a.inv_count : (diff < 0.f ? -a.inv_count : 0.f);
         l1 += fabsf(diff);
       }
+    }
+  }
+  if (a.pair_counts) {
+    unsigned long long e = n_eval, c = n_comp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(a.pair_counts, e);
+      atomicAdd(a.pair_counts + 1, c);
     }
   }
   if (a.targets) {

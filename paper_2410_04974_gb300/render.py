@@ -38,7 +38,7 @@ def camera_array(cams):
 
 
 def make_settings(tile=(16, 16), batch=256, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
-                  spin_budget=0) -> _lib.Settings:
+                  spin_budget=0, loss_norm=0.0, count_pairs=False) -> _lib.Settings:
     s = _lib.Settings()
     s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
     s.batch = int(batch)
@@ -47,6 +47,8 @@ def make_settings(tile=(16, 16), batch=256, lambda_opa=0.35, bg=(1.0, 1.0, 1.0),
         s.bg[i] = float(bg[i])
     s.store_aux = 1 if store_aux else 0
     s.spin_budget = int(spin_budget)
+    s.loss_norm = float(loss_norm)
+    s.count_pairs = 1 if count_pairs else 0
     return s
 
 
@@ -78,14 +80,16 @@ class Renderer:
     """
 
     def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=256, lambda_opa=0.35,
-                 bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, device="cuda"):
+                 bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, loss_norm=0.0,
+                 count_pairs=False, device="cuda"):
         if not torch.cuda.is_available():
             raise _lib.SixDGSError("sixdgs needs a CUDA device; there is no CPU path")
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cameras = list(cameras)
-        self.settings = make_settings(tile, batch, lambda_opa, bg, store_aux, spin_budget)
+        self.settings = make_settings(tile, batch, lambda_opa, bg, store_aux, spin_budget, loss_norm,
+                                      count_pairs)
         self.cams = camera_array(self.cameras)
         self._make_plan(dup_capacity)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
@@ -150,14 +154,36 @@ class Renderer:
                                               _ptr(grad_images), _ptr(loss), _ptr(self.status),
                                               self._stream(stream)), "sixdgs_raster_fwd")
 
-    def raster_bwd(self, params, images, grad_images, grads, stream=None):
+    def raster_bwd(self, params, images, grad_images, grads, accumulate=False, stream=None):
         ws, nb = self._wsargs()
         sc = self.scene_struct(params)
         _lib.check(self.lib.sixdgs_raster_bwd(ctypes.byref(self.plan), ctypes.byref(sc), ws, nb,
                                               _ptr(images), _ptr(grad_images), _ptr(grads["mu_p"]),
                                               _ptr(grads["mu_d"]), _ptr(grads["l_raw"]),
                                               _ptr(grads["opacity_logit"]), _ptr(grads["sh"]),
-                                              _ptr(self.status), self._stream(stream)), "sixdgs_raster_bwd")
+                                              int(accumulate), _ptr(self.status), self._stream(stream)),
+                   "sixdgs_raster_bwd")
+
+    def blend_bwd(self, images, grad_images, stream=None):
+        ws, nb = self._wsargs()
+        _lib.check(self.lib.sixdgs_blend_bwd(ctypes.byref(self.plan), ws, nb, _ptr(images), _ptr(grad_images),
+                                             _ptr(self.status), self._stream(stream)), "sixdgs_blend_bwd")
+
+    def project_bwd(self, params, grads, accumulate=False, stream=None):
+        ws, nb = self._wsargs()
+        sc = self.scene_struct(params)
+        _lib.check(self.lib.sixdgs_project_bwd(ctypes.byref(self.plan), ctypes.byref(sc), ws, nb,
+                                               _ptr(grads["mu_p"]), _ptr(grads["mu_d"]), _ptr(grads["l_raw"]),
+                                               _ptr(grads["opacity_logit"]), _ptr(grads["sh"]), int(accumulate),
+                                               _ptr(self.status), self._stream(stream)), "sixdgs_project_bwd")
+
+    def set_cameras(self, cameras):
+        """Swap in cameras of the same sizes (same plan and workspace)."""
+        cameras = list(cameras)
+        if [(int(c.height), int(c.width)) for c in cameras] != self.sizes:
+            raise _lib.SixDGSError("set_cameras needs cameras of the planned sizes")
+        self.cameras = cameras
+        self.cams = camera_array(cameras)
 
     def new_grads(self, params):
         return {k: torch.empty_like(params[k]) for k in PARAM_NAMES}
@@ -190,9 +216,9 @@ class Renderer:
             return images, gi, loss
         return images
 
-    def backward(self, params, images, grad_images, stream=None, grads=None):
+    def backward(self, params, images, grad_images, stream=None, grads=None, accumulate=False):
         grads = grads if grads is not None else self.new_grads(params)
-        self.raster_bwd(params, images, grad_images, grads, stream)
+        self.raster_bwd(params, images, grad_images, grads, accumulate=accumulate, stream=stream)
         return grads
 
     def raise_status(self, st=None):
@@ -207,7 +233,13 @@ class Renderer:
         return self.ws[off:off + nbytes].view(dtype)
 
     def counts(self):
-        return self._section(_lib.WS_COUNTS, torch.int32, 4).cpu().numpy().astype(np.int64)
+        """[visible pairs, duplicates K] of the last bin_sort."""
+        return self._section(_lib.WS_COUNTS, torch.int32, 2).cpu().numpy().astype(np.int64)
+
+    def pair_counts(self):
+        """[evaluated, compositing] (pixel, entry) pairs of the last raster_fwd
+        (needs count_pairs=True)."""
+        return self._section(_lib.WS_COUNTS, torch.int64, 4)[2:].cpu().numpy()
 
     def records(self):
         return self._section(_lib.WS_REC, torch.float32, 12 * int(self.plan.n_pairs)).view(-1, 12)
