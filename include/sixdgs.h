@@ -259,6 +259,37 @@ sixdgs_status sixdgs_project_bwd(const sixdgs_plan* plan, const sixdgs_scene* sc
                                  float* grad_sh, int32_t accumulate, int32_t* status_dev,
                                  sixdgs_stream_t stream);
 
+/* Forward render without any caller-provided workspace.  The paper has no
+ * counterpart: this is a convenience of this library.
+ *
+ * For callers that cannot allocate device memory: code embedded in a host
+ * application whose own allocator owns the device memory (plugins, engines
+ * with a fixed budget), or loops that must never call cudaMalloc.  It runs
+ * the same work as sixdgs_condition_project + sixdgs_bin_sort +
+ * sixdgs_raster_fwd (no loss) and writes the same images, but keeps the
+ * frame's workspace in one array of SIXDGS_STATIC_WS_BYTES (32 MiB) that
+ * lives in the library's device memory.  Every GPU that loads the library
+ * holds that array until the process exits.  The call allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Limits: the frame's plan (sixdgs_plan_init with the default duplicate
+ * capacity) must need at most SIXDGS_STATIC_WS_BYTES of workspace, about
+ * 170,000 (camera, Gaussian) pairs (e.g. 171,520 Gaussians seen by one
+ * 800x800 camera, or 42,896 Gaussians by four 256x256 cameras); larger
+ * frames are refused with SIXDGS_ERR_WORKSPACE before anything is launched.  The array is
+ * shared by all calls on a device and keeps the last call's contents (each
+ * call clears what it needs); calls that overlap on the GPU (different
+ * streams or threads, same device) race on it, so serialise them.  The
+ * first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Arguments are those of the staged calls; scene and images as there.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA; device status as the staged calls. */
+#define SIXDGS_STATIC_WS_BYTES (32u << 20)
+sixdgs_status sixdgs_render_fwd_static(int64_t n, int32_t sh_degree, const sixdgs_scene* scene,
+                                       const sixdgs_camera* cams, int32_t n_cams,
+                                       const sixdgs_settings* settings, float* images_dev,
+                                       int32_t* status_dev, sixdgs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

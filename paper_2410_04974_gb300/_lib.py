@@ -56,10 +56,14 @@ EXPORTS = {
                                     c_void_p, c_int32, c_void_p, c_void_p]),
     "sixdgs_blend_bwd": (c_int32, [ctypes.POINTER(Plan), c_void_p, c_size_t, c_void_p, c_void_p,
                                    c_void_p, c_void_p]),
+    "sixdgs_render_fwd_static": (c_int32, [c_int64, c_int32, ctypes.POINTER(Scene), ctypes.POINTER(Camera),
+                                           c_int32, ctypes.POINTER(Settings), c_void_p, c_void_p, c_void_p]),
     "sixdgs_project_bwd": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), c_void_p, c_size_t,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                      c_void_p, c_void_p]),
 }
+
+STATIC_WS_BYTES = 32 << 20   # SIXDGS_STATIC_WS_BYTES
 
 _LIB = None
 
