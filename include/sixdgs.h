@@ -145,7 +145,9 @@ typedef struct sixdgs_plan {
 enum {
   SIXDGS_WS_CAMS = 0,      /* per-camera records                              */
   SIXDGS_WS_REC = 1,       /* n_pairs x 12 float: u, v, qa, qb, qc, lo, r, g,
-                              b, depth, radius, 0 of each (view, Gaussian)     */
+                              b, hx, hy, depth of each (view, Gaussian):
+                              log2 alpha = qa dx^2 + qb dx dy + qc dy^2 + lo,
+                              (hx, hy) the alpha >= 1/255 bounding box       */
   SIXDGS_WS_NTILES = 2,    /* n_pairs x uint32 tiles touched (0 = culled)      */
   SIXDGS_WS_RECT = 3,      /* n_pairs x 4 uint16 tile rect x0, x1, y0, y1      */
   SIXDGS_WS_DEPTHKEY = 4,  /* n_pairs x uint32                                 */

@@ -41,9 +41,11 @@ struct __align__(16) CamRec {
 static_assert(sizeof(CamRec) == 128, "CamRec must stay 128 bytes");
 
 // Record of one (view, Gaussian) pair, consumed by the blend (48 bytes).
-//  a = (u, v, qa, qb), b = (qc, lo, r, g), c = (b, depth, radius, 0)
+//  a = (u, v, qa, qb), b = (qc, lo, r, g), c = (b, hx, hy, depth)
 // with q(dx, dy) = qa dx^2 + qb dx dy + qc dy^2 + lo = log2(alpha_cond) +
-// log2(e) * (-1/2 Delta^T conic Delta), Delta = (u - px, v - py).
+// log2(e) * (-1/2 Delta^T conic Delta), Delta = (u - px, v - py), and
+// (hx, hy) the half-extents of the box around (u, v) outside which
+// q < log2(1/255) (the entry is skipped at every pixel there).
 struct __align__(16) PairRec {
   float4 a, b, c;
 };

@@ -120,10 +120,18 @@ __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
                 if (k < K) s += beta[k][c] * Y[k];
               rgb[c] = sigmoidf_(s);
             }
+            // Bounding box of the alpha >= 1/255 ellipse {Delta^T conic Delta <=
+            // 2 ln(255 alpha_cond)}: half-extents sqrt(L2 * Sigma_2D,ii), widened
+            // by a margin far above FP32 rounding so that culling with it never
+            // drops an entry that a pixel would composite.
+            const float lo = log2f(alpha_cond);
+            const float L2 = 2.f * kLn2 * fmaxf(lo - kQMin, 0.f);
+            const float hx = sqrtf(L2 * ca) * 1.0001f + 0.01f;
+            const float hy = sqrtf(L2 * cc) * 1.0001f + 0.01f;
             PairRec rec;
             rec.a = make_float4(u, w, -0.5f * kLog2e * con_a, -kLog2e * con_b);
-            rec.b = make_float4(-0.5f * kLog2e * con_c, log2f(alpha_cond), rgb[0], rgb[1]);
-            rec.c = make_float4(rgb[2], t[2], radius, 0.f);
+            rec.b = make_float4(-0.5f * kLog2e * con_c, lo, rgb[0], rgb[1]);
+            rec.c = make_float4(rgb[2], hx, hy, t[2]);
             a.rec[pair] = rec;
             float4* gr = reinterpret_cast<float4*>(a.grad_rec) + pair * 3;
             gr[0] = gr[1] = gr[2] = make_float4(0.f, 0.f, 0.f, 0.f);

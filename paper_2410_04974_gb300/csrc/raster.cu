@@ -2,12 +2,17 @@
 // reverse (the 3DGS rasteriser that 6DGS section 4.4 keeps after slicing).
 //
 // One CTA per global tile (all cameras' tiles in one grid, so cameras of
-// different resolutions share a launch), one thread per pixel.  The tile's
-// sorted list is walked in batches: each batch of pair records is gathered
-// into shared memory by the whole CTA, then every thread composites its
-// pixel against it.  A CTA leaves as soon as __syncthreads_count reports
-// every pixel saturated; in the backward pass a warp leaves a batch as soon
-// as all its lanes are done.
+// different resolutions share a launch), one thread per pixel; each warp
+// owns an 8x4 sub-block of the tile.  The tile's sorted list is walked in
+// batches: each batch of pair records is gathered into shared memory by the
+// whole CTA; then every warp tests 32 entries at a time against its
+// sub-block (lane-parallel box test with the entry's alpha >= 1/255 box,
+// ballot) and composites its pixels only against the entries that can reach
+// them, in list order.  An entry a warp passes over would be skipped at
+// every pixel of its sub-block (q < log2(1/255)), so the result is the same
+// as walking every entry at every pixel.  A CTA leaves as soon as
+// __syncthreads_count reports every pixel saturated; a warp leaves a batch
+// as soon as all its lanes are done.
 //
 // Per entry and pixel:  q = qa dx^2 + qb dx dy + qc dy^2 + lo  (log2 alpha),
 // skipped when q < log2(1/255); alpha = min(0.99, 2^q); stop (excluding the
@@ -17,6 +22,9 @@
 #include "kernels.cuh"
 
 namespace sixdgs {
+
+constexpr int kSubW = 8;   // warp sub-block: 8 x 4 pixels
+constexpr int kSubH = 4;
 
 __device__ __forceinline__ int find_camera(const CamRec* cams, int n_cams, uint32_t gt) {
   int lo = 0, hi = n_cams - 1;
@@ -28,23 +36,64 @@ __device__ __forceinline__ int find_camera(const CamRec* cams, int n_cams, uint3
   return lo;
 }
 
+// Pixel of this thread and the pixel-centre box of its warp's sub-block.
+struct PixelMap {
+  int px, py;
+  float x0, x1, y0, y1;   // pixel centres spanned by the warp
+};
+
+__device__ __forceinline__ PixelMap map_pixel(int tile_w, int tx, int ty, int tile_h) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub_per_row = tile_w / kSubW;
+  const int sx = (warp % sub_per_row) * kSubW, sy = (warp / sub_per_row) * kSubH;
+  PixelMap m;
+  m.px = tx * tile_w + sx + (lane % kSubW);
+  m.py = ty * tile_h + sy + (lane / kSubW);
+  m.x0 = (float)(tx * tile_w + sx) + 0.5f;
+  m.x1 = m.x0 + (float)(kSubW - 1);
+  m.y0 = (float)(ty * tile_h + sy) + 0.5f;
+  m.y1 = m.y0 + (float)(kSubH - 1);
+  return m;
+}
+
+// Can entry (u, v, hx, hy) reach any pixel centre of the sub-block?
+__device__ __forceinline__ bool reaches(const PixelMap& m, float4 a, float4 c) {
+  return (a.x + c.y >= m.x0) && (a.x - c.y <= m.x1) && (a.y + c.z >= m.y0) && (a.y - c.z <= m.y1);
+}
+
+__device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, int cnt, float4* s_a,
+                                           float4* s_b, float4* s_c) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const uint32_t p = a.sorted[start + i];
+    if (p < a.n_pairs) {
+      const PairRec& r = a.rec[p];
+      s_a[i] = r.a;
+      s_b[i] = r.b;
+      s_c[i] = make_float4(r.c.x, r.c.y, r.c.z, __uint_as_float(p));
+    } else {  // unreachable for a consistent sort: an entry that reaches no pixel
+      s_a[i] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
+      s_b[i] = make_float4(0.f, -1e30f, 0.f, 0.f);
+      s_c[i] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0u));
+    }
+  }
+}
+
 __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
   const int B = a.batch;
   float4* s_a = s_mem;
   float4* s_b = s_mem + B;
-  float* s_c = reinterpret_cast<float*>(s_mem + 2 * B);
+  float4* s_c = s_mem + 2 * B;
   __shared__ float s_red[16];
 
   const uint32_t gt = blockIdx.x;
   const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
   const uint32_t local = gt - (uint32_t)cam.tile_offset;
-  const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-  const int px = tx * a.tile_w + (int)threadIdx.x % a.tile_w;
-  const int py = ty * a.tile_h + (int)threadIdx.x / a.tile_w;
-  const bool inside = px < cam.width && py < cam.height;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
+  const bool inside = pm.px < cam.width && pm.py < cam.height;
+  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
   const uint2 range = a.ranges[gt];
+  const int lane = threadIdx.x & 31;
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   bool done = !inside;
@@ -53,22 +102,17 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const uint32_t p = a.sorted[start + i];
-      if (p < a.n_pairs) {
-        const PairRec& r = a.rec[p];
-        s_a[i] = r.a;
-        s_b[i] = r.b;
-        s_c[i] = r.c.x;
-      } else {  // unreachable for a consistent sort; an entry that is always skipped
-        s_a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_b[i] = make_float4(0.f, -1e30f, 0.f, 0.f);
-        s_c[i] = 0.f;
-      }
-    }
+    load_batch(a, start, cnt, s_a, s_b, s_c);
     __syncthreads();
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
+    if (__all_sync(0xffffffffu, done)) continue;
+    for (int base = 0; base < cnt; base += 32) {
+      const int jl = base + lane;
+      const bool rel = jl < cnt && reaches(pm, s_a[jl], s_c[jl]);
+      uint32_t mask = __ballot_sync(0xffffffffu, rel);
+      while (mask) {
+        const int j = base + __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (done) continue;
         const float4 ra = s_a[j], rb = s_b[j];
         float dx, dy;
         const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
@@ -79,15 +123,16 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
         if (test_T < kTMin) {
           done = true;
           walked = start - range.x + j;
-          break;
+          continue;
         }
-        ++n_comp;
         const float w = __fmul_rn(alpha, T);
         C0 = __fmaf_rn(rb.z, w, C0);
         C1 = __fmaf_rn(rb.w, w, C1);
-        C2 = __fmaf_rn(s_c[j], w, C2);
+        C2 = __fmaf_rn(s_c[j].x, w, C2);
         T = test_T;
+        ++n_comp;
       }
+      if (__all_sync(0xffffffffu, done)) break;
     }
   }
 
@@ -97,7 +142,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
     C1 = __fmaf_rn(T, a.bg[1], C1);
     C2 = __fmaf_rn(T, a.bg[2], C2);
     const int64_t hw = (int64_t)cam.width * cam.height;
-    const int64_t pix = (int64_t)py * cam.width + px;
+    const int64_t pix = (int64_t)pm.py * cam.width + pm.px;
     float* img = a.images + 3 * cam.pixel_base;
     img[pix] = C0;
     img[hw + pix] = C1;
@@ -122,14 +167,14 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
       e += __shfl_xor_sync(0xffffffffu, e, o);
       c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       atomicAdd(a.pair_counts, e);
       atomicAdd(a.pair_counts + 1, c);
     }
   }
   if (a.targets) {
     l1 = warp_sum(l1);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = l1;
+    if (lane == 0) s_red[threadIdx.x >> 5] = l1;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
@@ -139,11 +184,36 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   }
 }
 
-// Vector reduction of the atomics into the (view, Gaussian) gradient record.
-__device__ __forceinline__ void red_add_v4(float* addr, float x, float y, float z, float w) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(x), "f"(y), "f"(z),
-               "f"(w)
-               : "memory");
+// Sum of 8 per-lane values over the warp with 9 shuffles instead of 40:
+// each butterfly step sends half of the values a lane still carries to its
+// partner and keeps the other half, so after the xor-16/8/4 steps lane l
+// carries only value 4*b4 + 2*b3 + b2 (bits of l), summed over the lanes
+// that differ in those bits, and the xor-2/1 steps finish the sum.  Returns
+// the total of that value; its index is (l >> 2) & 7.
+__device__ __forceinline__ float warp_sum8_transposed(const float* v, int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float h[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b4 ? v[i + 4] : v[i];
+    const float send = b4 ? v[i] : v[i + 4];
+    h[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float q[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b3 ? h[i + 2] : h[i];
+    const float send = b3 ? h[i] : h[i + 2];
+    q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float r = (b2 ? q[1] : q[0]) + __shfl_xor_sync(0xffffffffu, b2 ? q[0] : q[1], 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+__device__ __forceinline__ void red_add(float* addr, float x) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
 }
 
 __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
@@ -151,17 +221,14 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
   const int B = a.batch;
   float4* s_a = s_mem;
   float4* s_b = s_mem + B;
-  float* s_c = reinterpret_cast<float*>(s_mem + 2 * B);
-  uint32_t* s_p = reinterpret_cast<uint32_t*>(s_c + B);
+  float4* s_c = s_mem + 2 * B;
 
   const uint32_t gt = blockIdx.x;
   const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
   const uint32_t local = gt - (uint32_t)cam.tile_offset;
-  const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-  const int px = tx * a.tile_w + (int)threadIdx.x % a.tile_w;
-  const int py = ty * a.tile_h + (int)threadIdx.x / a.tile_w;
-  const bool inside = px < cam.width && py < cam.height;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
+  const bool inside = pm.px < cam.width && pm.py < cam.height;
+  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
   const uint2 range = a.ranges[gt];
   const int lane = threadIdx.x & 31;
 
@@ -169,7 +236,7 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
   uint32_t bound = range.y - range.x;
   if (inside) {
     const int64_t hw = (int64_t)cam.width * cam.height;
-    const int64_t pix = (int64_t)py * cam.width + px;
+    const int64_t pix = (int64_t)pm.py * cam.width + pm.px;
     const float* img = a.images_in + 3 * cam.pixel_base;
     const float* gi = a.grad_in + 3 * cam.pixel_base;
 #pragma unroll
@@ -185,95 +252,84 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      uint32_t p = a.sorted[start + i];
-      if (p < a.n_pairs) {
-        const PairRec& r = a.rec[p];
-        s_a[i] = r.a;
-        s_b[i] = r.b;
-        s_c[i] = r.c.x;
-      } else {  // unreachable for a consistent sort; an entry that is always skipped
-        p = 0;
-        s_a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_b[i] = make_float4(0.f, -1e30f, 0.f, 0.f);
-        s_c[i] = 0.f;
-      }
-      s_p[i] = p;
-    }
+    load_batch(a, start, cnt, s_a, s_b, s_c);
     __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
-      if (__all_sync(0xffffffffu, done)) break;
-      float g[9];
+    if (__all_sync(0xffffffffu, done)) continue;
+    for (int base = 0; base < cnt; base += 32) {
+      const int jl = base + lane;
+      const bool rel = jl < cnt && reaches(pm, s_a[jl], s_c[jl]);
+      uint32_t mask = __ballot_sync(0xffffffffu, rel);
+      while (mask) {
+        const int j = base + __ffs(mask) - 1;
+        mask &= mask - 1;
+        float g[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) g[k] = 0.f;
-      bool contrib = false;
-      if (!done) {
-        const uint32_t idx = start - range.x + j;
-        if (!a.recompute && idx >= bound) {
-          done = true;
-        } else {
-          const float4 ra = s_a[j], rb = s_b[j];
-          float dx, dy;
-          const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
-          if (q >= kQMin) {
-            const float e = ex2_approx(q);
-            const float alpha = fminf(kAlphaMax, e);
-            const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            if (a.recompute && test_T < kTMin) {
-              done = true;
-            } else {
-              const float rgb2 = s_c[j];
-              const float w = __fmul_rn(alpha, T);
-              P0 = __fmaf_rn(rb.z, w, P0);
-              P1 = __fmaf_rn(rb.w, w, P1);
-              P2 = __fmaf_rn(rgb2, w, P2);
-              // colour behind this entry (background included)
-              const float S0 = Cf[0] - P0, S1 = Cf[1] - P1, S2 = Cf[2] - P2;
-              const float inv1ma = 1.f / (1.f - alpha);
-              g[6] = dC[0] * w;
-              g[7] = dC[1] * w;
-              g[8] = dC[2] * w;
-              const float dLda = dC[0] * (rb.z * T - S0 * inv1ma) + dC[1] * (rb.w * T - S1 * inv1ma) +
-                                 dC[2] * (rgb2 * T - S2 * inv1ma);
-              const float dq = (e <= kAlphaMax) ? dLda * alpha * kLn2 : 0.f;
-              g[0] = dq * (2.f * ra.z * dx + ra.w * dy);
-              g[1] = dq * (ra.w * dx + 2.f * rb.x * dy);
-              g[2] = dq * dx * dx;
-              g[3] = dq * dx * dy;
-              g[4] = dq * dy * dy;
-              g[5] = dq;
-              T = test_T;
-              contrib = true;
+        for (int k = 0; k < 9; ++k) g[k] = 0.f;
+        bool contrib = false;
+        if (!done) {
+          const uint32_t idx = start - range.x + j;
+          if (!a.recompute && idx >= bound) {
+            done = true;
+          } else {
+            const float4 ra = s_a[j], rb = s_b[j];
+            float dx, dy;
+            const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
+            if (q >= kQMin) {
+              const float e = ex2_approx(q);
+              const float alpha = fminf(kAlphaMax, e);
+              const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+              if (a.recompute && test_T < kTMin) {
+                done = true;
+              } else {
+                const float rgb2 = s_c[j].x;
+                const float w = __fmul_rn(alpha, T);
+                P0 = __fmaf_rn(rb.z, w, P0);
+                P1 = __fmaf_rn(rb.w, w, P1);
+                P2 = __fmaf_rn(rgb2, w, P2);
+                // colour behind this entry (background included)
+                const float S0 = Cf[0] - P0, S1 = Cf[1] - P1, S2 = Cf[2] - P2;
+                const float inv1ma = 1.f / (1.f - alpha);
+                g[6] = dC[0] * w;
+                g[7] = dC[1] * w;
+                g[8] = dC[2] * w;
+                const float dLda = dC[0] * (rb.z * T - S0 * inv1ma) + dC[1] * (rb.w * T - S1 * inv1ma) +
+                                   dC[2] * (rgb2 * T - S2 * inv1ma);
+                const float dq = (e <= kAlphaMax) ? dLda * alpha * kLn2 : 0.f;
+                g[0] = dq * (2.f * ra.z * dx + ra.w * dy);
+                g[1] = dq * (ra.w * dx + 2.f * rb.x * dy);
+                g[2] = dq * dx * dx;
+                g[3] = dq * dx * dy;
+                g[4] = dq * dy * dy;
+                g[5] = dq;
+                T = test_T;
+                contrib = true;
+              }
             }
           }
         }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) g[k] = warp_sum(g[k]);
-        if (lane == 0) {
-          float* dst = a.grad_rec + (size_t)s_p[j] * 12;
-          red_add_v4(dst, g[0], g[1], g[2], g[3]);
-          red_add_v4(dst + 4, g[4], g[5], g[6], g[7]);
-          atomicAdd(dst + 8, g[8]);
+        if (__any_sync(0xffffffffu, contrib)) {
+          const float s8 = warp_sum8_transposed(g, lane);
+          const float s9 = warp_sum(g[8]);
+          float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
+          if ((lane & 3) == 0) red_add(dst + ((lane >> 2) & 7), s8);
+          if (lane == 0) red_add(dst + 8, s9);
         }
       }
+      if (__all_sync(0xffffffffu, done)) break;
     }
   }
 }
 
-static int blend_smem(int batch, bool bwd) {
-  return batch * (2 * (int)sizeof(float4) + (int)sizeof(float) + (bwd ? (int)sizeof(uint32_t) : 0));
-}
+static int blend_smem(int batch) { return batch * 3 * (int)sizeof(float4); }
 
 void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  blend_fwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, blend_smem(a.batch, false), stream>>>(a);
+  blend_fwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, blend_smem(a.batch), stream>>>(a);
 }
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  blend_bwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, blend_smem(a.batch, true), stream>>>(a);
+  blend_bwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, blend_smem(a.batch), stream>>>(a);
 }
 
 }  // namespace sixdgs

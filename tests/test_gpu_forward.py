@@ -54,8 +54,15 @@ def _check_records(r, scene, cams, st, view):
     np.testing.assert_allclose(rec[both, 5], np.log2(o["ac"][both]), atol=2e-4)
     np.testing.assert_allclose(rec[both, 6:8], o["rgb"][both, :2], atol=2e-6)
     np.testing.assert_allclose(rec[both, 8], o["rgb"][both, 2], atol=2e-6)
-    np.testing.assert_allclose(rec[both, 9], o["depth"][both], rtol=2e-6)
-    np.testing.assert_allclose(rec[both, 10], o["radius"][both], rtol=2e-4)
+    np.testing.assert_allclose(rec[both, 11], o["depth"][both], rtol=2e-6)
+    # (hx, hy): box of the alpha >= 1/255 ellipse, never smaller than the exact one
+    con = o["conic"][both]
+    det = con[:, 0] * con[:, 2] - con[:, 1] ** 2
+    L2 = 2.0 * np.log(255.0 * o["ac"][both])
+    hx_exact = np.sqrt(L2 * con[:, 2] / det)
+    hy_exact = np.sqrt(L2 * con[:, 0] / det)
+    assert np.all(rec[both, 9] >= hx_exact) and np.all(rec[both, 10] >= hy_exact)
+    assert np.all(rec[both, 9] <= 1.001 * hx_exact + 0.02) and np.all(rec[both, 10] <= 1.001 * hy_exact + 0.02)
     return prep, (cert, poss, sure, maybe)
 
 
