@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--config", type=int, default=2, help="workload index (2 = headline)")
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count (smaller runs)")
     ap.add_argument("--tile", type=int, nargs=2, default=(16, 16))
-    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--store-aux", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -367,7 +367,7 @@ def run_ours(args, world, rank, local):
     rc = sx.Renderer(w.scene.n, w.scene.sh_degree, cams, count_pairs=True, **kw)
     rc.forward(params)
     torch.cuda.synchronize()
-    n_eval, n_comp = [int(x) for x in rc.pair_counts()]
+    n_eval, n_comp, n_warp = [int(x) for x in rc.pair_counts()]
     del rc
     clk = clocks.summary()
     dom = max(("raster_fwd", "blend_bwd"), key=lambda s: stages[s])
@@ -381,7 +381,8 @@ def run_ours(args, world, rank, local):
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_basis": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                               f"{peak_clock:.0f} MHz (median SM clock under load)",
-                "pairs_evaluated": n_eval, "pairs_compositing": n_comp, "kernel_ms": round(dom_ms, 4)}
+                "pairs_evaluated": n_eval, "pairs_compositing": n_comp, "warp_entries": n_warp,
+                "kernel_ms": round(dom_ms, 4)}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0) ----
     cpu = None

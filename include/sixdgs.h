@@ -107,7 +107,7 @@ typedef struct sixdgs_settings {
   int32_t tile_w;      /* screen tile width  in {8, 16, 32}                   */
   int32_t tile_h;      /* screen tile height in {8, 16}                       */
   int32_t batch;       /* list entries staged per shared-memory batch, a
-                          multiple of 32 in [32, 256]                         */
+                          multiple of 32 in [32, 1024] (48 bytes each)        */
   float lambda_opa;    /* Eq. pdfv2: f_cond = exp(-lambda_opa * D), [0, 1]    */
   float bg[3];         /* background colour                                   */
   int32_t store_aux;   /* 1: raster_fwd stores the per-pixel walk length and
@@ -152,8 +152,9 @@ enum {
   SIXDGS_WS_RECT = 3,      /* n_pairs x 4 uint16 tile rect x0, x1, y0, y1      */
   SIXDGS_WS_DEPTHKEY = 4,  /* n_pairs x uint32                                 */
   SIXDGS_WS_COUNTS = 5,    /* uint32 visible pairs, uint32 duplicates (K),
-                              8 bytes unused, uint64 evaluated and uint64
-                              compositing (pixel, entry) pairs (count_pairs) */
+                              8 bytes unused, then (count_pairs) uint64
+                              evaluated and compositing (pixel, entry) pairs
+                              and uint64 (warp, entry) pairs walked          */
   SIXDGS_WS_SORTED = 6,    /* dup_capacity x uint32 pair index, sorted by
                               (global tile, depth, Gaussian id)               */
   SIXDGS_WS_RANGES = 7,    /* total_tiles x uint32[2] [start, end) in SORTED  */

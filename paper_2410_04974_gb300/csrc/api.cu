@@ -132,7 +132,7 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   if (sh_degree < 0 || sh_degree > 3) return SIXDGS_ERR_INVALID_ARG;
   if (!(st->tile_w == 8 || st->tile_w == 16 || st->tile_w == 32)) return SIXDGS_ERR_INVALID_ARG;
   if (!(st->tile_h == 8 || st->tile_h == 16)) return SIXDGS_ERR_INVALID_ARG;
-  if (st->batch < 32 || st->batch > 256 || st->batch % 32) return SIXDGS_ERR_INVALID_ARG;
+  if (st->batch < 32 || st->batch > 1024 || st->batch % 32) return SIXDGS_ERR_INVALID_ARG;
   if (!(st->lambda_opa >= 0.f) || !(st->lambda_opa <= 1.f)) return SIXDGS_ERR_INVALID_ARG;
   const int64_t n_pairs = (int64_t)n_cams * n;
   if (n_pairs >= ((int64_t)1 << 31)) return SIXDGS_ERR_INVALID_ARG;
@@ -183,7 +183,7 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   take(SIXDGS_WS_NWALK, st->store_aux ? pixels * 4 : 0);
   // cleared at the start of every bin_sort
   plan->off[WS_ZERO] = o;
-  take(SIXDGS_WS_COUNTS, 32);
+  take(SIXDGS_WS_COUNTS, 48);
   take(WS_COUNTERS, 64 * 4);
   take(WS_SCAN_C, scan_tiles * 8);
   take(WS_SCAN_E, scan_tiles * 8);

@@ -2,8 +2,8 @@
 // reverse (the 3DGS rasteriser that 6DGS section 4.4 keeps after slicing).
 //
 // One CTA per global tile (all cameras' tiles in one grid, so cameras of
-// different resolutions share a launch), one thread per pixel; each warp
-// owns an 8x4 sub-block of the tile.  The tile's sorted list is walked in
+// different resolutions share a launch); each warp owns an 8x4 sub-block of
+// the tile, one pixel per lane.  The tile's sorted list is walked in
 // batches: each batch of pair records is gathered into shared memory by the
 // whole CTA; then every warp tests 32 entries at a time against its
 // sub-block (lane-parallel box test with the entry's alpha >= 1/255 box,
@@ -18,6 +18,9 @@
 // skipped when q < log2(1/255); alpha = min(0.99, 2^q); stop (excluding the
 // entry) when T (1 - alpha) < 1e-4; C += c alpha T; T *= (1 - alpha).
 // Explicit rounding intrinsics make the backward replay bit-identical.
+// The forward culls with the alpha box only (its per-entry work is too cheap
+// for the exact test to pay off); the backward, whose per-entry work is
+// several times larger, also applies the exact quadratic test.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -56,9 +59,35 @@ __device__ __forceinline__ PixelMap map_pixel(int tile_w, int tx, int ty, int ti
   return m;
 }
 
-// Can entry (u, v, hx, hy) reach any pixel centre of the sub-block?
-__device__ __forceinline__ bool reaches(const PixelMap& m, float4 a, float4 c) {
-  return (a.x + c.y >= m.x0) && (a.x - c.y <= m.x1) && (a.y + c.z >= m.y0) && (a.y - c.z <= m.y1);
+// Can the entry have q >= log2(1/255) at some pixel centre of the warp's
+// sub-block?  First the entry's alpha box (u, v, hx, hy); with kExact also
+// the maximum of the concave quadratic q over the sub-block's pixel-centre
+// rectangle: the entry's centre if it lies inside, else the best point of
+// the four edges (vertex of q along each edge, clamped to the edge).  The
+// continuous maximum bounds every pixel centre's q, and the 1e-3 margin (in
+// log2 units) is far above FP32 rounding, so no pixel that would composite
+// the entry is ever passed over.
+template <bool kExact>
+__device__ __forceinline__ bool reaches(const PixelMap& m, float4 a, float4 b, float4 c) {
+  if (!((a.x + c.y >= m.x0) && (a.x - c.y <= m.x1) && (a.y + c.z >= m.y0) && (a.y - c.z <= m.y1)))
+    return false;
+  if (!kExact) return true;
+  const float dx0 = a.x - m.x1, dx1 = a.x - m.x0;   // dx = u - x over the sub-block
+  const float dy0 = a.y - m.y1, dy1 = a.y - m.y0;
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+  const float qa = a.z, qb = a.w, qc = b.x;
+  const float kx = -0.5f * qb / qc, ky = -0.5f * qb / qa;
+  float best = -INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dx = e ? dx1 : dx0;
+    const float dy = fminf(fmaxf(kx * dx, dy0), dy1);
+    best = fmaxf(best, (qa * dx + qb * dy) * dx + qc * dy * dy);
+    const float ey = e ? dy1 : dy0;
+    const float ex = fminf(fmaxf(ky * ey, dx0), dx1);
+    best = fmaxf(best, (qa * ex + qb * ey) * ex + qc * ey * ey);
+  }
+  return best + b.y >= kQMin - 1e-3f;
 }
 
 __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, int cnt, float4* s_a,
@@ -78,6 +107,7 @@ __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, i
   }
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
   const int B = a.batch;
@@ -98,7 +128,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   bool done = !inside;
   uint32_t walked = range.y - range.x;
-  uint32_t n_eval = 0, n_comp = 0;
+  uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
@@ -107,8 +137,9 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
     if (__all_sync(0xffffffffu, done)) continue;
     for (int base = 0; base < cnt; base += 32) {
       const int jl = base + lane;
-      const bool rel = jl < cnt && reaches(pm, s_a[jl], s_c[jl]);
+      const bool rel = jl < cnt && reaches<false>(pm, s_a[jl], s_b[jl], s_c[jl]);
       uint32_t mask = __ballot_sync(0xffffffffu, rel);
+      if (kCount) n_warp += __popc(mask);
       while (mask) {
         const int j = base + __ffs(mask) - 1;
         mask &= mask - 1;
@@ -116,7 +147,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
         const float4 ra = s_a[j], rb = s_b[j];
         float dx, dy;
         const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
-        ++n_eval;
+        if (kCount) ++n_eval;
         if (q < kQMin) continue;
         const float alpha = fminf(kAlphaMax, ex2_approx(q));
         const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
@@ -130,7 +161,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
         C1 = __fmaf_rn(rb.w, w, C1);
         C2 = __fmaf_rn(s_c[j].x, w, C2);
         T = test_T;
-        ++n_comp;
+        if (kCount) ++n_comp;
       }
       if (__all_sync(0xffffffffu, done)) break;
     }
@@ -149,18 +180,16 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
     img[2 * hw + pix] = C2;
     if (a.nwalk) a.nwalk[cam.pixel_base + pix] = walked;
     if (a.targets) {
-      const float* tg = a.targets + 3 * cam.pixel_base;
-      float* gi = a.grad_images + 3 * cam.pixel_base;
-      const float c[3] = {C0, C1, C2};
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        const float diff = c[ch] - tg[ch * hw + pix];
-        gi[ch * hw + pix] = diff > 0.f ? a.inv_count : (diff < 0.f ? -a.inv_count : 0.f);
-        l1 += fabsf(diff);
-      }
+      const float* tg = a.targets + 3 * cam.pixel_base + pix;
+      float* gi = a.grad_images + 3 * cam.pixel_base + pix;
+      const float d0 = C0 - tg[0], d1 = C1 - tg[hw], d2 = C2 - tg[2 * hw];
+      gi[0] = d0 > 0.f ? a.inv_count : (d0 < 0.f ? -a.inv_count : 0.f);
+      gi[hw] = d1 > 0.f ? a.inv_count : (d1 < 0.f ? -a.inv_count : 0.f);
+      gi[2 * hw] = d2 > 0.f ? a.inv_count : (d2 < 0.f ? -a.inv_count : 0.f);
+      l1 = fabsf(d0) + fabsf(d1) + fabsf(d2);
     }
   }
-  if (a.pair_counts) {
+  if (kCount) {
     unsigned long long e = n_eval, c = n_comp;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -170,6 +199,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
     if (lane == 0) {
       atomicAdd(a.pair_counts, e);
       atomicAdd(a.pair_counts + 1, c);
+      atomicAdd(a.pair_counts + 2, (unsigned long long)n_warp);
     }
   }
   if (a.targets) {
@@ -257,7 +287,7 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
     if (__all_sync(0xffffffffu, done)) continue;
     for (int base = 0; base < cnt; base += 32) {
       const int jl = base + lane;
-      const bool rel = jl < cnt && reaches(pm, s_a[jl], s_c[jl]);
+      const bool rel = jl < cnt && reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl]);
       uint32_t mask = __ballot_sync(0xffffffffu, rel);
       while (mask) {
         const int j = base + __ffs(mask) - 1;
@@ -322,14 +352,30 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
 
 static int blend_smem(int batch) { return batch * 3 * (int)sizeof(float4); }
 
+// Batches near or above 48 KB of shared memory (with the kernels' static
+// shared memory) need the opt-in limit.
+static void allow_smem(const void* fn, int bytes) {
+  if (bytes > 40 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  blend_fwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, blend_smem(a.batch), stream>>>(a);
+  const int smem = blend_smem(a.batch);
+  const int threads = a.tile_w * a.tile_h;
+  if (a.pair_counts) {
+    allow_smem((const void*)blend_fwd_kernel<true>, smem);
+    blend_fwd_kernel<true><<<(unsigned)total_tiles, threads, smem, stream>>>(a);
+  } else {
+    allow_smem((const void*)blend_fwd_kernel<false>, smem);
+    blend_fwd_kernel<false><<<(unsigned)total_tiles, threads, smem, stream>>>(a);
+  }
 }
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  blend_bwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, blend_smem(a.batch), stream>>>(a);
+  const int smem = blend_smem(a.batch);
+  allow_smem((const void*)blend_bwd_kernel, smem);
+  blend_bwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, smem, stream>>>(a);
 }
 
 }  // namespace sixdgs

@@ -37,7 +37,7 @@ def camera_array(cams):
     return arr
 
 
-def make_settings(tile=(16, 16), batch=256, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
+def make_settings(tile=(16, 16), batch=512, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
                   spin_budget=0, loss_norm=0.0, count_pairs=False) -> _lib.Settings:
     s = _lib.Settings()
     s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
@@ -79,7 +79,7 @@ class Renderer:
     one backward() on the same stream.
     """
 
-    def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=256, lambda_opa=0.35,
+    def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=512, lambda_opa=0.35,
                  bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, loss_norm=0.0,
                  count_pairs=False, device="cuda"):
         if not torch.cuda.is_available():
@@ -237,9 +237,9 @@ class Renderer:
         return self._section(_lib.WS_COUNTS, torch.int32, 2).cpu().numpy().astype(np.int64)
 
     def pair_counts(self):
-        """[evaluated, compositing] (pixel, entry) pairs of the last raster_fwd
-        (needs count_pairs=True)."""
-        return self._section(_lib.WS_COUNTS, torch.int64, 4)[2:].cpu().numpy()
+        """[evaluated, compositing] (pixel, entry) pairs and (warp, entry)
+        pairs walked by the last raster_fwd (needs count_pairs=True)."""
+        return self._section(_lib.WS_COUNTS, torch.int64, 5)[2:].cpu().numpy()
 
     def records(self):
         return self._section(_lib.WS_REC, torch.float32, 12 * int(self.plan.n_pairs)).view(-1, 12)

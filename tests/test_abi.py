@@ -68,7 +68,7 @@ def test_plan_mixed_resolutions_and_tile_shapes():
     assert plan.total_pixels == sum(c.width * c.height for c in w.cameras)
 
 
-@pytest.mark.parametrize("kw", [dict(tile=(12, 16)), dict(tile=(16, 32)), dict(batch=48), dict(batch=512),
+@pytest.mark.parametrize("kw", [dict(tile=(12, 16)), dict(tile=(16, 32)), dict(batch=48), dict(batch=2048),
                                 dict(lambda_opa=1.5)])
 def test_plan_rejects_bad_settings(kw):
     code, _ = _plan(synth.ring_cameras(1, 64, 64), **kw)
