@@ -106,20 +106,24 @@ __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
           bool finite = isfinite(u) && isfinite(w) && isfinite(radius) && isfinite(con_a) &&
                         isfinite(con_b) && isfinite(con_c);
           if (!finite) raise_status(a.status, SIXDGS_ERR_NONFINITE);
+          // ---- colour (section 4.2) ----
+          float Y[kMaxShCoeffs];
+          sh_basis(a.sh_degree, d[0], d[1], d[2], Y);
+          float rgb[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxShCoeffs; ++k)
+              if (k < K) s += beta[k][c] * Y[k];
+            rgb[c] = sigmoidf_(s);
+          }
+          if (finite && !(isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]))) {
+            finite = false;
+            raise_status(a.status, SIXDGS_ERR_NONFINITE);
+          }
           if (finite && x0 < x1 && y0 < y1) {
             ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
-            // ---- colour (section 4.2) ----
-            float Y[kMaxShCoeffs];
-            sh_basis(a.sh_degree, d[0], d[1], d[2], Y);
-            float rgb[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              float s = 0.f;
-#pragma unroll
-              for (int k = 0; k < kMaxShCoeffs; ++k)
-                if (k < K) s += beta[k][c] * Y[k];
-              rgb[c] = sigmoidf_(s);
-            }
             // Bounding box of the alpha >= 1/255 ellipse {Delta^T conic Delta <=
             // 2 ln(255 alpha_cond)}: half-extents sqrt(L2 * Sigma_2D,ii), widened
             // by a margin far above FP32 rounding so that culling with it never

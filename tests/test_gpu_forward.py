@@ -32,8 +32,8 @@ def _check_records(r, scene, cams, st, view):
     """Per (view, Gaussian) record vs the oracle's slice/colour/projection."""
     prep = PT.oracle_prep(scene, cams[view], st)
     n = scene.n
-    rec = r.records().cpu().numpy()[view * n:(view + 1) * n].astype(np.float64)
-    nt = r.ntiles().cpu().numpy()[view * n:(view + 1) * n]
+    rec = r.records()[view * n:(view + 1) * n].cpu().numpy().astype(np.float64)
+    nt = r.ntiles()[view * n:(view + 1) * n].cpu().numpy()
     cert, poss, sure, maybe = PT.membership_sets(prep, cams[view], st)
     gvis = nt > 0
     certain_vis = sure & (cert[:, 0] < cert[:, 1]) & (cert[:, 2] < cert[:, 3])
