@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --tile/--batch as given instead of the autotuner's pick")
+    ap.add_argument("--tune-tiles", action="store_true",
+                    help="let the autotuner also choose the tile shape (changes the render's tile lists)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many batched steps eagerly and exit (for ncu)")
     return ap.parse_args()
@@ -178,6 +182,12 @@ class ClockSampler:
 # our arm
 # --------------------------------------------------------------------------
 
+def launches_per_frame(plan, n_cams):
+    """Kernels of ours one fwd+bwd frame launches: camera upload (one per 48
+    cameras), projection, compaction, depth passes, emission, tile passes,
+    ranges, blend forward, blend backward, SH backward, geometry backward."""
+    return (n_cams + 47) // 48 + 1 + 1 + plan.depth_passes + 1 + plan.tile_passes + 1 + 1 + 1 + 1 + 1
+
 def build_inputs(args):
     w = synth.make_workload(args.config, n_override=args.n or None)
     target_scene = synth.perturb(w.scene, synth.target_seed(args.config))
@@ -187,18 +197,28 @@ def build_inputs(args):
 def run_ours(args, world, rank, local):
     import paper_2410_04974_gb300 as sx
 
+    from paper_2410_04974_gb300 import autotune
+
     dev = torch.device("cuda", local)
     w, tscene = build_inputs(args)
     cams = w.cameras
     V = len(cams)
-    kw = dict(tile=tuple(args.tile), batch=args.batch, lambda_opa=w.lambda_opa, bg=w.bg, store_aux=args.store_aux)
+    params = sx.params_to_device(w.scene, dev)
+    base_kw = dict(lambda_opa=w.lambda_opa, bg=w.bg, store_aux=args.store_aux)
+    tuned = None
+    if args.no_autotune or args.profile_steps:
+        kw = dict(tile=tuple(args.tile), batch=args.batch, persistent=True, **base_kw)
+    else:
+        tiles = ((16, 16), (16, 8), (32, 8), (8, 16), (32, 16)) if args.tune_tiles else (tuple(args.tile),)
+        space = autotune.candidate_space(tiles=tiles, batches=(256, 512, 1024), persistent=(True, False))
+        tuned = autotune.tune(params, w.scene.n, w.scene.sh_degree, cams, space=space, **base_kw)
+        kw = dict(tile=tuple(tuned["tile"]), batch=tuned["batch"], persistent=tuned["persistent"], **base_kw)
     # targets: render the perturbed scene once (untimed)
     rt = sx.Renderer(tscene.n, tscene.sh_degree, cams, **kw)
     targets = rt.forward(sx.params_to_device(tscene, dev))
     torch.cuda.synchronize()
     del rt
 
-    params = sx.params_to_device(w.scene, dev)
     r = sx.Renderer(w.scene.n, w.scene.sh_degree, cams, **kw)
     images = r.forward(params)                       # sizes the duplicate capacity
     torch.cuda.synchronize()
@@ -304,37 +324,49 @@ def run_ours(args, world, rank, local):
     plain = None
     equiv = None
     if not args.no_plain:
-        rp = sx.Renderer(w.scene.n, w.scene.sh_degree, [cams[0]], loss_norm=3.0 * r.total_pixels, **kw)
-        per_view = [slice(3 * sum(h * wd for (h, wd) in r.sizes[:v]), 3 * sum(h * wd for (h, wd) in r.sizes[:v + 1]))
-                    for v in range(V)]
-        grads_p = rp.new_grads(params)
+        # one single-camera plan per distinct resolution; the loss is normalised
+        # over the whole batch so losses and gradients equal the batched ones
+        plain_r = {}
+        for c in cams:
+            key = (c.width, c.height)
+            if key not in plain_r:
+                plain_r[key] = sx.Renderer(w.scene.n, w.scene.sh_degree, [c], loss_norm=3.0 * r.total_pixels, **kw)
+        offs = np.cumsum([0] + [3 * h * wd for (h, wd) in r.sizes])
+        per_view = [slice(int(offs[v]), int(offs[v + 1])) for v in range(V)]
+        grads_p = r.new_grads(params)
+        loss_p = torch.zeros(1, dtype=torch.float64, device=dev)
 
         def plain_step():
-            rp.status.zero_()
-            rp.loss.zero_()
+            loss_p.zero_()
+            for rr in plain_r.values():
+                rr.status.zero_()
             for v in range(V):
+                rp = plain_r[(cams[v].width, cams[v].height)]
                 rp.set_cameras([cams[v]])
                 sl = per_view[v]
                 rp.condition_project(params)
                 rp.bin_sort()
-                rp.raster_fwd(images[sl], targets[sl], gimg[sl], rp.loss)
+                rp.raster_fwd(images[sl], targets[sl], gimg[sl], loss_p)
                 rp.raster_bwd(params, images[sl], gimg[sl], grads_p, accumulate=v > 0)
 
         for _ in range(max(3, args.warmup // 2)):
             plain_step()
         torch.cuda.synchronize()
-        rp.raise_status()
+        for rr in plain_r.values():
+            rr.raise_status()
         t_plain = timed(plain_step, max(10, args.steps // 4))
-        rp.raise_status()
+        for rr in plain_r.values():
+            rr.raise_status()
         ms_plain = max_over_ranks(sum(t_plain) / len(t_plain), world)
+        rp0 = next(iter(plain_r.values()))
         plain = {"value": V * 1000.0 / ms_plain * world, "unit": UNIT, "ms_per_step": ms_plain,
-                 "launches_per_step": V * 16, "graph": False}
+                 "launches_per_step": V * launches_per_frame(rp0.plan, 1), "graph": False}
         g_rel = {k: float((grads_p[k] - grads_batched[k]).norm() / grads_batched[k].norm().clamp_min(1e-30))
                  for k in grads_p}
         equiv = {"image_max_abs": float((images - img_batched).abs().max()),
-                 "loss_abs": abs(float(rp.loss.item()) - loss_batched),
+                 "loss_abs": abs(float(loss_p.item()) - loss_batched),
                  "grad_rel_l2_max": max(g_rel.values())}
-        del rp
+        del plain_r
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -395,16 +427,18 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms_batched, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n_gaussians": w.scene.n, "views": V,
-                   "resolution": f"{cams[0].width}x{cams[0].height}", "tile": list(args.tile),
-                   "batch": args.batch, "store_aux": bool(args.store_aux), "sh_degree": w.scene.sh_degree,
+                   "resolution": sorted({f"{c.width}x{c.height}" for c in cams}), "tile": list(kw["tile"]),
+                   "batch": kw["batch"], "store_aux": bool(args.store_aux), "sh_degree": w.scene.sh_degree,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed steps (256 MiB write outside the timed events)",
-                   "graph": True, "visible_pairs": int(counts[0]), "duplicates": int(counts[1]),
-                   "dup_capacity": int(cap)},
+                   "graph": True, "persistent_blend": bool(kw["persistent"]),
+                   "visible_pairs": int(counts[0]), "duplicates": int(counts[1]), "dup_capacity": int(cap),
+                   "autotuned": None if tuned is None else {k: tuned[k] for k in ("tile", "batch", "persistent",
+                                                                                 "ms", "cached")}},
         "plain": plain, "speedup_vs_plain": round(plain["ms_per_step"] / ms_batched, 3) if plain else None,
         "batched_vs_plain": equiv, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
         "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-        "gpu_launches": 16 * args.steps,
+        "gpu_launches": launches_per_frame(r.plan, V) * args.steps,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "loss": loss_batched,
     }

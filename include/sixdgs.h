@@ -122,6 +122,10 @@ typedef struct sixdgs_settings {
                           per plan)                                           */
   int32_t count_pairs; /* 1: raster_fwd also counts evaluated and compositing
                           (pixel, list entry) pairs into SIXDGS_WS_COUNTS     */
+  int32_t persistent;  /* 1: the blend kernels run as one resident grid whose
+                          CTAs take the tiles of all cameras from a device
+                          queue; 0: one CTA per tile                          */
+  int32_t _pad;
 } sixdgs_settings;
 
 /* Sizes and workspace layout of one frame, filled by sixdgs_plan_init. */

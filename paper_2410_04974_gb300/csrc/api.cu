@@ -388,6 +388,8 @@ static BlendArgs blend_args(const sixdgs_plan* p, void* ws) {
   a.pair_counts = p->settings.count_pairs
                       ? reinterpret_cast<unsigned long long*>(ws_ptr<char>(ws, p, SIXDGS_WS_COUNTS) + 16)
                       : nullptr;
+  a.tile_queue = p->settings.persistent ? ws_ptr<uint32_t>(ws, p, WS_COUNTERS) + 32 : nullptr;
+  a.total_tiles = (uint32_t)p->total_tiles;
   return a;
 }
 

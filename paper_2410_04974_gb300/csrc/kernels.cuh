@@ -107,6 +107,9 @@ struct BlendArgs {
   const float* grad_in;
   float* grad_rec;          // n_pairs x 12
   int32_t recompute;        // 1: re-derive the stop; 0: use nwalk
+  // persistent mode: tiles are taken from this counter (NULL: one CTA per tile)
+  uint32_t* tile_queue;
+  uint32_t total_tiles;
 };
 
 struct ProjectBwdArgs {

@@ -21,6 +21,8 @@
 // The forward culls with the alpha box only (its per-entry work is too cheap
 // for the exact test to pay off); the backward, whose per-entry work is
 // several times larger, also applies the exact quadratic test.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -107,16 +109,15 @@ __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, i
   }
 }
 
+// Forward blend of global tile gt by the calling CTA.
 template <bool kCount>
-__global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
-  extern __shared__ float4 s_mem[];
+__device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
   const int B = a.batch;
   float4* s_a = s_mem;
   float4* s_b = s_mem + B;
   float4* s_c = s_mem + 2 * B;
   __shared__ float s_red[16];
 
-  const uint32_t gt = blockIdx.x;
   const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
   const uint32_t local = gt - (uint32_t)cam.tile_offset;
   const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
@@ -246,14 +247,13 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
 }
 
-__global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
-  extern __shared__ float4 s_mem[];
+// Backward blend of global tile gt by the calling CTA.
+__device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
   const int B = a.batch;
   float4* s_a = s_mem;
   float4* s_b = s_mem + B;
   float4* s_c = s_mem + 2 * B;
 
-  const uint32_t gt = blockIdx.x;
   const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
   const uint32_t local = gt - (uint32_t)cam.tile_offset;
   const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
@@ -350,6 +350,44 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
   }
 }
 
+// One CTA per tile (grid = tiles), or persistent: a grid of as many CTAs as
+// fit on the GPU at once, each taking tiles from a device counter until all
+// cameras' tiles are done.
+template <bool kCount>
+__global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
+  extern __shared__ float4 s_mem[];
+  if (!a.tile_queue) {
+    blend_fwd_tile<kCount>(a, blockIdx.x, s_mem);
+    return;
+  }
+  __shared__ uint32_t s_next;
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(a.tile_queue, 1u);
+    __syncthreads();
+    const uint32_t gt = s_next;
+    if (gt >= a.total_tiles) break;
+    blend_fwd_tile<kCount>(a, gt, s_mem);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
+  extern __shared__ float4 s_mem[];
+  if (!a.tile_queue) {
+    blend_bwd_tile(a, blockIdx.x, s_mem);
+    return;
+  }
+  __shared__ uint32_t s_next;
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(a.tile_queue, 1u);
+    __syncthreads();
+    const uint32_t gt = s_next;
+    if (gt >= a.total_tiles) break;
+    blend_bwd_tile(a, gt, s_mem);
+    __syncthreads();
+  }
+}
+
 static int blend_smem(int batch) { return batch * 3 * (int)sizeof(float4); }
 
 // Batches near or above 48 KB of shared memory (with the kernels' static
@@ -358,24 +396,39 @@ static void allow_smem(const void* fn, int bytes) {
   if (bytes > 40 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
-  if (total_tiles == 0) return;
+// CTAs of `fn` resident on the whole GPU at once (the persistent grid).
+static int resident_grid(const void* fn, int threads, int smem, int64_t tiles) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  const int64_t g = (int64_t)std::max(per_sm, 1) * std::max(sms, 1);
+  return (int)std::min<int64_t>(g, tiles);
+}
+
+template <typename K>
+static void launch_blend(K kernel, const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   const int smem = blend_smem(a.batch);
   const int threads = a.tile_w * a.tile_h;
-  if (a.pair_counts) {
-    allow_smem((const void*)blend_fwd_kernel<true>, smem);
-    blend_fwd_kernel<true><<<(unsigned)total_tiles, threads, smem, stream>>>(a);
+  allow_smem((const void*)kernel, smem);
+  if (a.tile_queue) {
+    cudaMemsetAsync(a.tile_queue, 0, sizeof(uint32_t), stream);
+    const int grid = resident_grid((const void*)kernel, threads, smem, total_tiles);
+    kernel<<<grid, threads, smem, stream>>>(a);
   } else {
-    allow_smem((const void*)blend_fwd_kernel<false>, smem);
-    blend_fwd_kernel<false><<<(unsigned)total_tiles, threads, smem, stream>>>(a);
+    kernel<<<(unsigned)total_tiles, threads, smem, stream>>>(a);
   }
+}
+
+void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
+  if (total_tiles == 0) return;
+  if (a.pair_counts) launch_blend(blend_fwd_kernel<true>, a, total_tiles, stream);
+  else launch_blend(blend_fwd_kernel<false>, a, total_tiles, stream);
 }
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  const int smem = blend_smem(a.batch);
-  allow_smem((const void*)blend_bwd_kernel, smem);
-  blend_bwd_kernel<<<(unsigned)total_tiles, a.tile_w * a.tile_h, smem, stream>>>(a);
+  launch_blend(blend_bwd_kernel, a, total_tiles, stream);
 }
 
 }  // namespace sixdgs

@@ -40,10 +40,10 @@ def _grad_images_on_tiles(cams, views, st, per_view, seed):
     return g_imgs, tiles
 
 
-def _run(workload, views, tiles_fwd, tiles_bwd, seed):
+def _run(workload, views, tiles_fwd, tiles_bwd, seed, tile=(16, 16), batch=512, persistent=True):
     w = workload
-    st = O.Settings()
-    r = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras)
+    st = O.Settings(tile_w=tile[0], tile_h=tile[1])
+    r = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, tile=tile, batch=batch, persistent=persistent)
     params = sx.params_to_device(w.scene)
     img = r.forward(params)
     torch.cuda.synchronize()
@@ -67,8 +67,10 @@ def _run(workload, views, tiles_fwd, tiles_bwd, seed):
         assert np.all(gpu[k][..., ~touched] == 0.0), k
 
 
-def test_batched_500k_64_views_mixed_resolution():
-    _run(synth.make_workload(3), views=(0, 21, 63), tiles_fwd=6, tiles_bwd=3, seed=300)
+@pytest.mark.parametrize("tile,batch,persistent", [((16, 16), 512, True), ((16, 8), 256, False)])
+def test_batched_500k_64_views_mixed_resolution(tile, batch, persistent):
+    _run(synth.make_workload(3), views=(0, 21, 63), tiles_fwd=6, tiles_bwd=3, seed=300, tile=tile, batch=batch,
+         persistent=persistent)
 
 
 def test_view_dependent_2m_1080p_recompute_transmittance():
