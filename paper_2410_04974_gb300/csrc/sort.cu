@@ -284,56 +284,94 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(OnesweepArgs a) 
 
 // --------------------------------------------------------------------------
 // 3. Duplicate emission in depth order + tile-digit histograms
+//
+// Load-balanced: after the block's scan of the tile counts, consecutive
+// threads write consecutive duplicates; each finds the pair it belongs to by
+// binary search over the block's prefix sums in shared memory, so stores are
+// coalesced and no thread loops over a large rectangle alone.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(kScanThreads) emit_kernel(EmitArgs a) {
   __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+  __shared__ uint32_t s_start[kScanTile + 1];   // block-local first output of each element
+  __shared__ uint32_t s_pair[kScanTile];
+  __shared__ uint32_t s_base[kScanTile];        // key of the element's top-left tile
+  __shared__ uint32_t s_shape[kScanTile];       // rect width | tiles_x << 16
   __shared__ uint32_t s_hist[4 * 256];
   __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_excl;
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
   const uint32_t n_vis = *a.n_vis;
   const uint32_t num_tiles = (n_vis + kScanTile - 1) / kScanTile;
+  const int lane = threadIdx.x & 31;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= num_tiles) break;
-    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
-    uint32_t pair[kScanItems], cnt[kScanItems];
+    const uint32_t first = threadIdx.x * kScanItems;
+    const uint32_t base = tile * kScanTile + first;
+    uint32_t cnt[kScanItems];
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       bool valid = base + k < n_vis;
-      pair[k] = valid ? a.pairs[base + k] : 0u;
-      valid = valid && pair[k] < a.n_pairs;
-      cnt[k] = valid ? a.ntiles[pair[k]] : 0u;
+      const uint32_t p = valid ? a.pairs[base + k] : 0u;
+      valid = valid && p < a.n_pairs;
+      cnt[k] = valid ? a.ntiles[p] : 0u;
+      s_pair[first + k] = p;
+      if (cnt[k]) {
+        const CamRec& cam = a.cams[p / (uint32_t)a.n];
+        const ushort4 r = a.rect[p];
+        s_base[first + k] = (uint32_t)cam.tile_offset + (uint32_t)r.z * (uint32_t)cam.tiles_x + r.x;
+        s_shape[first + k] = (uint32_t)(r.y - r.x) | ((uint32_t)cam.tiles_x << 16);
+      }
       sum += cnt[k];
     }
     uint32_t total;
-    uint32_t excl = block_excl_scan<kScanThreads>(sum, total, s_warp);
+    uint32_t run = block_excl_scan<kScanThreads>(sum, total, s_warp);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      s_start[first + k] = run;
+      run += cnt[k];
+    }
+    if (threadIdx.x == 0) s_start[kScanTile] = total;
     if (threadIdx.x < 32) {
       unsigned long long e = scan_lookback(a.scan_state, tile, total, a.spin_budget, a.status);
       if (threadIdx.x == 0) s_excl = e;
     }
     __syncthreads();
-    uint64_t off = s_excl + excl;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      if (cnt[k] == 0u) continue;
-      const uint32_t p = pair[k];
-      const CamRec& cam = a.cams[p / (uint32_t)a.n];
-      const ushort4 r = a.rect[p];
-      for (uint32_t ty = r.z; ty < r.w; ++ty) {
-        for (uint32_t tx = r.x; tx < r.y; ++tx) {
-          const uint32_t key = (uint32_t)cam.tile_offset + ty * (uint32_t)cam.tiles_x + tx;
-          if (off < a.capacity) {
-            a.keys_out[off] = key;
-            a.vals_out[off] = p;
-            for (int q = 0; q < a.passes; ++q) atomicAdd(&s_hist[q * 256 + ((key >> (8 * q)) & 255u)], 1u);
-          }
-          ++off;
+    const unsigned long long gbase = s_excl;
+    for (uint32_t o0 = 0; o0 < total; o0 += kScanThreads) {
+      const uint32_t o = o0 + threadIdx.x;
+      const bool valid = o < total;
+      uint32_t key = 0xffffffffu, p = 0;
+      if (valid) {
+        // last element e with s_start[e] <= o (empty elements share starts)
+        int lo = 0, hi = kScanTile - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_start[mid] <= o) lo = mid;
+          else hi = mid - 1;
         }
+        const uint32_t local = o - s_start[lo];
+        const uint32_t shape = s_shape[lo];
+        const uint32_t w = shape & 0xffffu, tiles_x = shape >> 16;
+        const uint32_t row = local / w;
+        key = s_base[lo] + row * tiles_x + (local - row * w);
+        p = s_pair[lo];
+        const unsigned long long out = gbase + o;
+        if (out < a.capacity) {
+          a.keys_out[out] = key;
+          a.vals_out[out] = p;
+        } else {
+          key = 0xffffffffu;   // not stored: not counted
+        }
+      }
+      for (int q = 0; q < a.passes; ++q) {
+        const uint32_t d = key == 0xffffffffu ? 256u : (key >> (8 * q)) & 255u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[q * 256 + d], __popc(peers));
       }
     }
     if (tile == num_tiles - 1 && threadIdx.x == 0) {

@@ -38,7 +38,7 @@ def camera_array(cams):
 
 
 def make_settings(tile=(16, 16), batch=512, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
-                  spin_budget=0, loss_norm=0.0, count_pairs=False, persistent=True) -> _lib.Settings:
+                  spin_budget=0, loss_norm=0.0, count_pairs=False, persistent=False) -> _lib.Settings:
     s = _lib.Settings()
     s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
     s.batch = int(batch)
@@ -82,7 +82,7 @@ class Renderer:
 
     def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=512, lambda_opa=0.35,
                  bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, loss_norm=0.0,
-                 count_pairs=False, persistent=True, device="cuda"):
+                 count_pairs=False, persistent=False, device="cuda"):
         if not torch.cuda.is_available():
             raise _lib.SixDGSError("sixdgs needs a CUDA device; there is no CPU path")
         self.lib = _lib.load()

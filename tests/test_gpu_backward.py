@@ -36,8 +36,9 @@ def _compare(gpu, ref, tag, max_outliers=0.0):
     return report
 
 
-def _gpu_grads(scene, cams, g_imgs, tile=(16, 16), store_aux=False, lam=0.35):
-    r = sx.Renderer(scene.n, scene.sh_degree, cams, tile=tile, store_aux=store_aux, lambda_opa=lam)
+def _gpu_grads(scene, cams, g_imgs, tile=(16, 16), store_aux=False, lam=0.35, persistent=False):
+    r = sx.Renderer(scene.n, scene.sh_degree, cams, tile=tile, store_aux=store_aux, lambda_opa=lam,
+                    persistent=persistent)
     params = sx.params_to_device(scene)
     img = r.forward(params)
     g = r.backward(params, img, r.pack(g_imgs))
@@ -61,7 +62,7 @@ def test_multi_view_ragged_gradients_sum_over_views():
     cams = [synth.look_at_camera((4.0, 0.0, 0.5), 72, 56), synth.look_at_camera((0.0, -4.0, 0.0), 40, 88),
             synth.look_at_camera((-2.5, 2.5, 1.5), 64, 64)]
     g_imgs = synth.random_grad_images(cams, 8)
-    gpu, _ = _gpu_grads(scene, cams, g_imgs, tile=(8, 16))
+    gpu, _ = _gpu_grads(scene, cams, g_imgs, tile=(8, 16), persistent=True)
     ref = O.gradients(scene, cams, g_imgs, O.Settings(tile_w=8, tile_h=16))
     _compare(gpu, ref, "shell2k 3 views", max_outliers=2e-3)
 

@@ -19,9 +19,10 @@ def _settings(w, tile=(16, 16), lam=0.35, bg=(1.0, 1.0, 1.0)):
     return O.Settings(tile_w=tile[0], tile_h=tile[1], lambda_opa=lam, bg=bg)
 
 
-def _render(scene, cams, tile=(16, 16), batch=256, lam=0.35, bg=(1.0, 1.0, 1.0), store_aux=False):
+def _render(scene, cams, tile=(16, 16), batch=256, lam=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
+            persistent=False):
     r = sx.Renderer(scene.n, scene.sh_degree, cams, tile=tile, batch=batch, lambda_opa=lam, bg=bg,
-                    store_aux=store_aux)
+                    store_aux=store_aux, persistent=persistent)
     params = sx.params_to_device(scene)
     img = r.forward(params)
     torch.cuda.synchronize()
@@ -105,10 +106,11 @@ def _sample_tiles(cam, st, k, seed):
     return sorted(pick)
 
 
-def test_small_cube_scene_matches_oracle_everywhere():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_small_cube_scene_matches_oracle_everywhere(persistent):
     w = synth.make_workload(0)
     st = _settings(w)
-    r, params, img = _render(w.scene, w.cameras)
+    r, params, img = _render(w.scene, w.cameras, persistent=persistent)
     assert int(r.status.item()) == 0
     prep, member = _check_records(r, w.scene, w.cameras, st, 0)
     counts = r.counts()
@@ -118,14 +120,17 @@ def test_small_cube_scene_matches_oracle_everywhere():
     print(f"worst pixel error {worst:.2e}, borderline membership flips {flips}")
 
 
-@pytest.mark.parametrize("size,tile,batch", [((100, 70), (16, 16), 256), ((72, 40), (8, 8), 32),
-                                             ((130, 50), (32, 16), 128), ((64, 64), (16, 8), 64)])
-def test_ragged_images_and_tile_shapes(size, tile, batch):
+@pytest.mark.parametrize("size,tile,batch,persistent", [((100, 70), (16, 16), 256, False),
+                                                        ((72, 40), (8, 8), 32, True),
+                                                        ((130, 50), (32, 16), 128, False),
+                                                        ((64, 64), (16, 8), 64, True),
+                                                        ((90, 120), (8, 16), 1024, False)])
+def test_ragged_images_and_tile_shapes(size, tile, batch, persistent):
     scene = synth.scene_cube(1500, 31)
     scene.l_raw[:3] += math.log(2.0)
     cams = [synth.look_at_camera((4.0, 0.5, -0.3), size[0], size[1])]
     st = _settings(None, tile=tile, bg=(0.1, 0.5, 0.9))
-    r, params, img = _render(scene, cams, tile=tile, batch=batch, bg=(0.1, 0.5, 0.9))
+    r, params, img = _render(scene, cams, tile=tile, batch=batch, bg=(0.1, 0.5, 0.9), persistent=persistent)
     assert int(r.status.item()) == 0
     prep, member = _check_records(r, scene, cams, st, 0)
     _check_tiles(r, scene, cams, st, 0, _all_tiles(cams[0], st), prep, member,
