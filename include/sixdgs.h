@@ -163,7 +163,9 @@ enum {
                               (global tile, depth, Gaussian id)               */
   SIXDGS_WS_RANGES = 7,    /* total_tiles x uint32[2] [start, end) in SORTED  */
   SIXDGS_WS_NWALK = 8,     /* total_pixels x uint32 list entries walked       */
-  SIXDGS_WS_GRADREC = 9,   /* n_pairs x 12 float gradient of the record       */
+  SIXDGS_WS_GRADREC = 9,   /* n_pairs x 12 float: sums over pixels of g, g dx,
+                              g dy, g dx^2, g dx dy, g dy^2 (g = dL/dq / ln 2)
+                              and dL/d(r, g, b) of each (view, Gaussian)     */
   SIXDGS_WS_SORTEDKEY = 10 /* dup_capacity x uint32 global tile of SORTED     */
 };
 

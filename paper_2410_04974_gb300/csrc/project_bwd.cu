@@ -169,11 +169,17 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
     const float idet = 1.f / det;
     const float idet2 = idet * idet;
     // ---- record gradients -> conic and alpha_cond ----
-    const float du = ga.x, dvv = ga.y;
-    const float dcon_a = -0.5f * kLog2e * ga.z;
-    const float dcon_b = -kLog2e * ga.w;
-    const float dcon_c = -0.5f * kLog2e * gb.x;
-    const float dalpha_cond = gb.y / (alpha_cond * kLn2);   // lo = log2(alpha_cond)
+    // The blend leaves the moments M = sum over pixels of g, g dx, g dy,
+    // g dx^2, g dx dy, g dy^2 with g = (dL/dq) / ln 2 and
+    // q = qa dx^2 + qb dx dy + qc dy^2 + lo, dx = u - px, dy = v - py.
+    const float con_a0 = cc * idet, con_b0 = -cb * idet, con_c0 = ca * idet;
+    const float qa = -0.5f * kLog2e * con_a0, qb = -kLog2e * con_b0, qc = -0.5f * kLog2e * con_c0;
+    const float du = kLn2 * (2.f * qa * ga.x + qb * ga.y);
+    const float dvv = kLn2 * (qb * ga.x + 2.f * qc * ga.y);
+    const float dcon_a = -0.5f * kLog2e * kLn2 * ga.z;   // dq/dcon_a = -1/2 log2(e) dx^2
+    const float dcon_b = -kLog2e * kLn2 * ga.w;
+    const float dcon_c = -0.5f * kLog2e * kLn2 * gb.x;
+    const float dalpha_cond = gb.y / alpha_cond;         // lo = log2(alpha_cond): ln 2 cancels
     // conic = (cc, -cb, ca) / det  ->  (ca, cb, cc)
     const float d_ca = (-dcon_a * cc * cc + dcon_b * cb * cc - dcon_c * cb * cb) * idet2;
     const float d_cb = (2.f * dcon_a * cb * cc - dcon_b * (det + 2.f * cb * cb) + 2.f * dcon_c * ca * cb) * idet2;

@@ -276,7 +276,11 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
     }
     if (!a.recompute) bound = a.nwalk[cam.pixel_base + pix];
   }
-  float T = 1.f, P0 = 0.f, P1 = 0.f, P2 = 0.f;
+  // dL/dalpha_i = sum_c dC_c (c_i T_i - S_c / (1 - alpha_i)) with S the colour
+  // behind entry i, S_c = C_c - P_c (P the running front-to-back sum), so
+  // sum_c dC_c S_c = D0 - Q with D0 = dC . C and Q = dC . P kept as a scalar.
+  const float D0 = dC[0] * Cf[0] + dC[1] * Cf[1] + dC[2] * Cf[2];
+  float T = 1.f, Q = 0.f;
   bool done = !inside;
 
   for (uint32_t start = range.x; start < range.y; start += B) {
@@ -311,26 +315,23 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
               if (a.recompute && test_T < kTMin) {
                 done = true;
               } else {
-                const float rgb2 = s_c[j].x;
                 const float w = __fmul_rn(alpha, T);
-                P0 = __fmaf_rn(rb.z, w, P0);
-                P1 = __fmaf_rn(rb.w, w, P1);
-                P2 = __fmaf_rn(rgb2, w, P2);
-                // colour behind this entry (background included)
-                const float S0 = Cf[0] - P0, S1 = Cf[1] - P1, S2 = Cf[2] - P2;
-                const float inv1ma = 1.f / (1.f - alpha);
+                const float G = dC[0] * rb.z + dC[1] * rb.w + dC[2] * s_c[j].x;
+                Q = fmaf(w, G, Q);   // now includes this entry: D0 - Q is behind it
+                const float dLda = T * G - (D0 - Q) * __fdividef(1.f, 1.f - alpha);
+                // dL/dq / ln 2 (the factor ln 2 of d 2^q / dq is applied by the
+                // per-Gaussian backward); no gradient through the 0.99 clamp
+                const float dq = (e <= kAlphaMax) ? dLda * alpha : 0.f;
+                const float mx = dq * dx, my = dq * dy;
+                g[0] = mx;
+                g[1] = my;
+                g[2] = mx * dx;
+                g[3] = mx * dy;
+                g[4] = my * dy;
+                g[5] = dq;
                 g[6] = dC[0] * w;
                 g[7] = dC[1] * w;
                 g[8] = dC[2] * w;
-                const float dLda = dC[0] * (rb.z * T - S0 * inv1ma) + dC[1] * (rb.w * T - S1 * inv1ma) +
-                                   dC[2] * (rgb2 * T - S2 * inv1ma);
-                const float dq = (e <= kAlphaMax) ? dLda * alpha * kLn2 : 0.f;
-                g[0] = dq * (2.f * ra.z * dx + ra.w * dy);
-                g[1] = dq * (ra.w * dx + 2.f * rb.x * dy);
-                g[2] = dq * dx * dx;
-                g[3] = dq * dx * dy;
-                g[4] = dq * dy * dy;
-                g[5] = dq;
                 T = test_T;
                 contrib = true;
               }
