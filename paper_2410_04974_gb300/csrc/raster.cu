@@ -78,7 +78,7 @@ __device__ __forceinline__ bool reaches(const PixelMap& m, float4 a, float4 b, f
   const float dy0 = a.y - m.y1, dy1 = a.y - m.y0;
   if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
   const float qa = a.z, qb = a.w, qc = b.x;
-  const float kx = -0.5f * qb / qc, ky = -0.5f * qb / qa;
+  const float kx = __fdividef(-0.5f * qb, qc), ky = __fdividef(-0.5f * qb, qa);
   float best = -INFINITY;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -247,7 +247,10 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
 }
 
-// Backward blend of global tile gt by the calling CTA.
+// Backward blend of global tile gt by the calling CTA.  kRecompute: re-derive
+// the stop from the transmittance (no per-pixel state); otherwise walk each
+// pixel's stored number of entries.
+template <bool kRecompute>
 __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
   const int B = a.batch;
   float4* s_a = s_mem;
@@ -274,7 +277,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
       Cf[ch] = img[ch * hw + pix];
       dC[ch] = gi[ch * hw + pix];
     }
-    if (!a.recompute) bound = a.nwalk[cam.pixel_base + pix];
+    if (!kRecompute) bound = a.nwalk[cam.pixel_base + pix];
   }
   // dL/dalpha_i = sum_c dC_c (c_i T_i - S_c / (1 - alpha_i)) with S the colour
   // behind entry i, S_c = C_c - P_c (P the running front-to-back sum), so
@@ -302,7 +305,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
         bool contrib = false;
         if (!done) {
           const uint32_t idx = start - range.x + j;
-          if (!a.recompute && idx >= bound) {
+          if (!kRecompute && idx >= bound) {
             done = true;
           } else {
             const float4 ra = s_a[j], rb = s_b[j];
@@ -312,7 +315,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
               const float e = ex2_approx(q);
               const float alpha = fminf(kAlphaMax, e);
               const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-              if (a.recompute && test_T < kTMin) {
+              if (kRecompute && test_T < kTMin) {
                 done = true;
               } else {
                 const float w = __fmul_rn(alpha, T);
@@ -338,12 +341,20 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
             }
           }
         }
-        if (__any_sync(0xffffffffu, contrib)) {
-          const float s8 = warp_sum8_transposed(g, lane);
-          const float s9 = warp_sum(g[8]);
+        const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
+        if (cmask) {
           float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
-          if ((lane & 3) == 0) red_add(dst + ((lane >> 2) & 7), s8);
-          if (lane == 0) red_add(dst + 8, s9);
+          if (__popc(cmask) == 1) {   // one pixel: its own 9 atomics, no reduction
+            if (contrib) {
+#pragma unroll
+              for (int k = 0; k < 9; ++k) red_add(dst + k, g[k]);
+            }
+          } else {
+            const float s8 = warp_sum8_transposed(g, lane);
+            const float s9 = warp_sum(g[8]);
+            if ((lane & 3) == 0) red_add(dst + ((lane >> 2) & 7), s8);
+            if (lane == 0) red_add(dst + 8, s9);
+          }
         }
       }
       if (__all_sync(0xffffffffu, done)) break;
@@ -372,10 +383,11 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   }
 }
 
+template <bool kRecompute>
 __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
   if (!a.tile_queue) {
-    blend_bwd_tile(a, blockIdx.x, s_mem);
+    blend_bwd_tile<kRecompute>(a, blockIdx.x, s_mem);
     return;
   }
   __shared__ uint32_t s_next;
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
     __syncthreads();
     const uint32_t gt = s_next;
     if (gt >= a.total_tiles) break;
-    blend_bwd_tile(a, gt, s_mem);
+    blend_bwd_tile<kRecompute>(a, gt, s_mem);
     __syncthreads();
   }
 }
@@ -429,7 +441,8 @@ void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stre
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  launch_blend(blend_bwd_kernel, a, total_tiles, stream);
+  if (a.recompute) launch_blend(blend_bwd_kernel<true>, a, total_tiles, stream);
+  else launch_blend(blend_bwd_kernel<false>, a, total_tiles, stream);
 }
 
 }  // namespace sixdgs
