@@ -110,7 +110,7 @@ __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, i
 }
 
 // Forward blend of global tile gt by the calling CTA.
-template <bool kCount>
+template <bool kCount, bool kStore>
 __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
   const int B = a.batch;
   float4* s_a = s_mem;
@@ -144,25 +144,27 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, 
       while (mask) {
         const int j = base + __ffs(mask) - 1;
         mask &= mask - 1;
-        if (done) continue;
+        // Branch-free: a skipped (or finished) pixel takes alpha = 0, which
+        // leaves T and C bit-for-bit unchanged.
         const float4 ra = s_a[j], rb = s_b[j];
+        const float blue = s_c[j].x;
         float dx, dy;
         const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
-        if (kCount) ++n_eval;
-        if (q < kQMin) continue;
-        const float alpha = fminf(kAlphaMax, ex2_approx(q));
+        const bool vis = !done && q >= kQMin;
+        const float alpha = vis ? fminf(kAlphaMax, ex2_approx(q)) : 0.f;
         const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-        if (test_T < kTMin) {
-          done = true;
-          walked = start - range.x + j;
-          continue;
-        }
-        const float w = __fmul_rn(alpha, T);
+        const bool stop = test_T < kTMin;
+        const float w = stop ? 0.f : __fmul_rn(alpha, T);
         C0 = __fmaf_rn(rb.z, w, C0);
         C1 = __fmaf_rn(rb.w, w, C1);
-        C2 = __fmaf_rn(s_c[j].x, w, C2);
-        T = test_T;
-        if (kCount) ++n_comp;
+        C2 = __fmaf_rn(blue, w, C2);
+        T = stop ? T : test_T;
+        if (kStore && stop) walked = start - range.x + j;
+        if (kCount) {
+          n_eval += done ? 0u : 1u;
+          n_comp += (vis && !stop) ? 1u : 0u;
+        }
+        done = done || stop;
       }
       if (__all_sync(0xffffffffu, done)) break;
     }
@@ -179,7 +181,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, 
     img[pix] = C0;
     img[hw + pix] = C1;
     img[2 * hw + pix] = C2;
-    if (a.nwalk) a.nwalk[cam.pixel_base + pix] = walked;
+    if (kStore) a.nwalk[cam.pixel_base + pix] = walked;
     if (a.targets) {
       const float* tg = a.targets + 3 * cam.pixel_base + pix;
       float* gi = a.grad_images + 3 * cam.pixel_base + pix;
@@ -299,48 +301,40 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
       while (mask) {
         const int j = base + __ffs(mask) - 1;
         mask &= mask - 1;
+        // Branch-free, as in the forward: alpha = 0 for a pixel that skips
+        // the entry or is finished, which leaves T and Q unchanged and gives
+        // zero gradient.
+        const float4 ra = s_a[j], rb = s_b[j];
+        const float blue = s_c[j].x;
+        if (!kRecompute) done = done || (start - range.x + j >= bound);
+        float dx, dy;
+        const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
+        const bool vis = !done && q >= kQMin;
+        const float e = ex2_approx(q);
+        const float alpha = vis ? fminf(kAlphaMax, e) : 0.f;
+        const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        const bool stop = kRecompute && test_T < kTMin;
+        const bool contrib = vis && !stop;
+        const float w = contrib ? __fmul_rn(alpha, T) : 0.f;
+        const float G = dC[0] * rb.z + dC[1] * rb.w + dC[2] * blue;
+        Q = fmaf(w, G, Q);   // now includes this entry: D0 - Q is behind it
+        const float dLda = T * G - (D0 - Q) * __fdividef(1.f, 1.f - alpha);
+        // dL/dq / ln 2 (the factor ln 2 of d 2^q / dq is applied by the
+        // per-Gaussian backward); no gradient through the 0.99 clamp
+        const float dq = (contrib && e <= kAlphaMax) ? dLda * alpha : 0.f;
+        const float mx = dq * dx, my = dq * dy;
         float g[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) g[k] = 0.f;
-        bool contrib = false;
-        if (!done) {
-          const uint32_t idx = start - range.x + j;
-          if (!kRecompute && idx >= bound) {
-            done = true;
-          } else {
-            const float4 ra = s_a[j], rb = s_b[j];
-            float dx, dy;
-            const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
-            if (q >= kQMin) {
-              const float e = ex2_approx(q);
-              const float alpha = fminf(kAlphaMax, e);
-              const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-              if (kRecompute && test_T < kTMin) {
-                done = true;
-              } else {
-                const float w = __fmul_rn(alpha, T);
-                const float G = dC[0] * rb.z + dC[1] * rb.w + dC[2] * s_c[j].x;
-                Q = fmaf(w, G, Q);   // now includes this entry: D0 - Q is behind it
-                const float dLda = T * G - (D0 - Q) * __fdividef(1.f, 1.f - alpha);
-                // dL/dq / ln 2 (the factor ln 2 of d 2^q / dq is applied by the
-                // per-Gaussian backward); no gradient through the 0.99 clamp
-                const float dq = (e <= kAlphaMax) ? dLda * alpha : 0.f;
-                const float mx = dq * dx, my = dq * dy;
-                g[0] = mx;
-                g[1] = my;
-                g[2] = mx * dx;
-                g[3] = mx * dy;
-                g[4] = my * dy;
-                g[5] = dq;
-                g[6] = dC[0] * w;
-                g[7] = dC[1] * w;
-                g[8] = dC[2] * w;
-                T = test_T;
-                contrib = true;
-              }
-            }
-          }
-        }
+        g[0] = mx;
+        g[1] = my;
+        g[2] = mx * dx;
+        g[3] = mx * dy;
+        g[4] = my * dy;
+        g[5] = dq;
+        g[6] = dC[0] * w;
+        g[7] = dC[1] * w;
+        g[8] = dC[2] * w;
+        T = contrib ? test_T : T;
+        done = done || stop;
         const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
         if (cmask) {
           float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
@@ -365,11 +359,11 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
 // One CTA per tile (grid = tiles), or persistent: a grid of as many CTAs as
 // fit on the GPU at once, each taking tiles from a device counter until all
 // cameras' tiles are done.
-template <bool kCount>
+template <bool kCount, bool kStore>
 __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
   if (!a.tile_queue) {
-    blend_fwd_tile<kCount>(a, blockIdx.x, s_mem);
+    blend_fwd_tile<kCount, kStore>(a, blockIdx.x, s_mem);
     return;
   }
   __shared__ uint32_t s_next;
@@ -378,7 +372,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
     __syncthreads();
     const uint32_t gt = s_next;
     if (gt >= a.total_tiles) break;
-    blend_fwd_tile<kCount>(a, gt, s_mem);
+    blend_fwd_tile<kCount, kStore>(a, gt, s_mem);
     __syncthreads();
   }
 }
@@ -435,8 +429,13 @@ static void launch_blend(K kernel, const BlendArgs& a, int64_t total_tiles, cuda
 
 void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  if (a.pair_counts) launch_blend(blend_fwd_kernel<true>, a, total_tiles, stream);
-  else launch_blend(blend_fwd_kernel<false>, a, total_tiles, stream);
+  if (a.pair_counts) {
+    if (a.nwalk) launch_blend(blend_fwd_kernel<true, true>, a, total_tiles, stream);
+    else launch_blend(blend_fwd_kernel<true, false>, a, total_tiles, stream);
+  } else {
+    if (a.nwalk) launch_blend(blend_fwd_kernel<false, true>, a, total_tiles, stream);
+    else launch_blend(blend_fwd_kernel<false, false>, a, total_tiles, stream);
+  }
 }
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
