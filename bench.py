@@ -60,6 +60,39 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 
 
+# Sources of each profiled kernel: roofline "traffic" is taken from the
+# kernel's committed ncu summary (profiles/) only while these are unchanged.
+KERNEL_SOURCES = {
+    "blend_bwd_kernel": ["raster.cu"], "blend_fwd_kernel": ["raster.cu"],
+    "project_fwd_kernel": ["project.cu", "cond.cuh", "sh.cuh", "mat3.cuh"],
+    "onesweep_kernel": ["sort.cu"], "emit_kernel": ["sort.cu"],
+    "geom_bwd_kernel": ["project_bwd.cu", "cond.cuh", "mat3.cuh"],
+}
+
+
+def kernel_digest(kernel):
+    import hashlib
+    h = hashlib.sha1()
+    for f in ["common.cuh", "kernels.cuh"] + KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2410_04974_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from profiles/<kernel>_<workload>.md, or None when
+    there is no summary or the kernel's sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = dict(ln.split(": ", 1) for ln in text.splitlines() if ln.startswith(("traffic_bytes_per_launch", "source_digest")))
+    if fields.get("source_digest") != kernel_digest(kernel):
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,7 +240,7 @@ def run_ours(args, world, rank, local):
     base_kw = dict(lambda_opa=w.lambda_opa, bg=w.bg, store_aux=args.store_aux)
     tuned = None
     if args.no_autotune or args.profile_steps:
-        kw = dict(tile=tuple(args.tile), batch=args.batch, persistent=True, **base_kw)
+        kw = dict(tile=tuple(args.tile), batch=args.batch, persistent=False, **base_kw)
     else:
         tiles = ((16, 16), (16, 8), (32, 8), (8, 16), (32, 16)) if args.tune_tiles else (tuple(args.tile),)
         space = autotune.candidate_space(tiles=tiles, batches=(256, 512, 1024), persistent=(True, False))
@@ -410,7 +443,7 @@ def run_ours(args, world, rank, local):
     achieved = flops / (dom_ms * 1e-3) / 1e12
     kernel = {"raster_fwd": "blend_fwd_kernel", "blend_bwd": "blend_bwd_kernel"}[dom]
     roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kernel, w.name),
                 "peak_basis": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                               f"{peak_clock:.0f} MHz (median SM clock under load)",
                 "pairs_evaluated": n_eval, "pairs_compositing": n_comp, "warp_entries": n_warp,
