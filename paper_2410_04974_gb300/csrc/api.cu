@@ -390,13 +390,13 @@ static BlendArgs blend_args(const sixdgs_plan* p, void* ws) {
                       : nullptr;
   a.tile_queue = p->settings.persistent ? ws_ptr<uint32_t>(ws, p, WS_COUNTERS) + 32 : nullptr;
   a.total_tiles = (uint32_t)p->total_tiles;
+  a.spin_budget = spin_budget(p);
   return a;
 }
 
 sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, float* images_dev,
                                 const float* targets_dev, float* grad_images_dev, double* loss_dev,
                                 int32_t* status_dev, sixdgs_stream_t stream_) {
-  (void)status_dev;
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
   if (!images_dev) return SIXDGS_ERR_INVALID_ARG;
@@ -408,13 +408,13 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* p, void* ws, size_t ws_bytes,
   a.targets = targets_dev;
   a.grad_images = grad_images_dev;
   a.loss = loss_dev;
+  a.status = status_dev;
   launch_blend_fwd(a, p->total_tiles, reinterpret_cast<cudaStream_t>(stream_));
   return launch_status();
 }
 
 sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, const float* images_dev,
                                const float* grad_images_dev, int32_t* status_dev, sixdgs_stream_t stream_) {
-  (void)status_dev;
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
   if (!images_dev || !grad_images_dev) return SIXDGS_ERR_INVALID_ARG;
@@ -423,6 +423,7 @@ sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, 
   a.grad_in = grad_images_dev;
   a.grad_rec = ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
   a.recompute = p->settings.store_aux ? 0 : 1;
+  a.status = status_dev;
   launch_blend_bwd(a, p->total_tiles, reinterpret_cast<cudaStream_t>(stream_));
   return launch_status();
 }

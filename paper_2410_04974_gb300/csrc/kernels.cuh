@@ -110,6 +110,8 @@ struct BlendArgs {
   // persistent mode: tiles are taken from this counter (NULL: one CTA per tile)
   uint32_t* tile_queue;
   uint32_t total_tiles;
+  int64_t spin_budget;      // clock cycles a shared-memory ring wait may take
+  int32_t* status;
 };
 
 struct ProjectBwdArgs {
