@@ -58,6 +58,7 @@ FLOPS_COMP_BWD = 60
 MUFU_PER_COMP_FWD = 1
 SMS = 152
 FP32_LANES_PER_SM = 128
+SCALE_ROT_BYTES = (21 + 9 + 3) * 4
 
 
 # Sources of each profiled kernel: roofline "traffic" is taken from the
@@ -107,6 +108,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the scale / rotation and inference timings")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --tile/--batch as given instead of the autotuner's pick")
     ap.add_argument("--tune-tiles", action="store_true",
@@ -214,6 +216,150 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+
+def measure_scale_rotation(l_raw, flush, steps=20, big_n=1 << 22):
+    """Time the per-Gaussian scale / rotation extraction on the scene's own
+    Gaussians and on a 4M-Gaussian tiling of them (larger than L2).  Algorithmic
+    bytes per Gaussian: 21 raw Cholesky floats read, 9 + 3 floats written."""
+    peak = hbm_peak()
+    out = {}
+    reps = -(-big_n // l_raw.shape[1])
+    for name, raw in (("scene", l_raw), ("tiled_4M", l_raw.repeat(1, reps)[:, :big_n].contiguous())):
+        n = int(raw.shape[1])
+        for _ in range(3):
+            sx.scale_rotation(raw)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, status = sx.scale_rotation(raw)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        if int(status.item()) != 0:
+            raise RuntimeError(f"scale_rotation status {int(status.item())}")
+        ms = sum(times) / len(times)
+        gbs = n * SCALE_ROT_BYTES / (ms * 1e-3) / 1e9
+        out[name] = {"n": n, "ms": round(ms, 5), "gaussians_per_s": round(n / (ms * 1e-3), 1),
+                     "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                                  "frac": round(gbs / peak, 4), "peak_basis": "of measured"}}
+    return out
+
+
+def measure_inference(flush, reps=10, views=synth.TABLE2_TEST_VIEWS):
+    """Forward-only frames per second on scenes shaped like the paper's Table 2
+    (section 5.2): per scene, the view-independent slice state is cached once,
+    then each of `views` test cameras is rendered as its own frame (one
+    single-camera inference plan, frames back to back in one CUDA graph).
+    L2 is flushed before each timed replay of the `views` frames."""
+    import paper_2410_04974_gb300 as sx
+
+    out = []
+    for i in range(len(synth.TABLE2_SHAPES)):
+        w = synth.table2_workload(i, views=views)
+        params = sx.params_to_device(w.scene)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        params["cond_cache"] = sx.condition_cache(params)
+        e1.record()
+        torch.cuda.synchronize()
+        cache_ms = e0.elapsed_time(e1)
+        r = sx.Renderer(w.scene.n, w.scene.sh_degree, [w.cameras[0]], inference=True)
+        for cam in w.cameras:                      # size the duplicate capacity for every view
+            r.set_cameras([cam])
+            r.forward(params)
+        imgs = [r.new_images() for _ in w.cameras]
+
+        def frames():
+            for v, cam in enumerate(w.cameras):
+                r.set_cameras([cam])
+                r.condition_project(params)
+                r.bin_sort()
+                r.raster_fwd(imgs[v])
+
+        r.status.zero_()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            frames()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            frames()
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        r.raise_status()
+        times = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            graph.replay()
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        r.raise_status()
+        ms_frame = sum(times) / len(times) / len(w.cameras)
+        # per-stage split of one frame (eager launches)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        split = np.zeros(3)
+        for cam in w.cameras:
+            r.set_cameras([cam])
+            ev[0].record()
+            r.condition_project(params)
+            ev[1].record()
+            r.bin_sort()
+            ev[2].record()
+            r.raster_fwd(imgs[0])
+            ev[3].record()
+            torch.cuda.synchronize()
+            split += [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
+        split /= len(w.cameras)
+        # all test views as one batched inference plan
+        rb = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, inference=True)
+        img_b = rb.forward(params)
+        tb = []
+        for _ in range(max(3, reps // 2)):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            rb.condition_project(params)
+            rb.bin_sort()
+            rb.raster_fwd(img_b)
+            b.record()
+            torch.cuda.synchronize()
+            tb.append(a.elapsed_time(b))
+        rb.raise_status()
+        ms_batch = sum(tb) / len(tb)
+        name, n, side_px, kind, paper_fps = synth.TABLE2_SHAPES[i]
+        out.append({"workload": name, "n_gaussians": n, "resolution": f"{side_px}x{side_px}",
+                    "fps": round(1000.0 / ms_frame, 1), "ms_per_frame": round(ms_frame, 4),
+                    "stage_ms": {"condition_project": round(split[0], 4), "bin_sort": round(split[1], 4),
+                                 "raster_fwd": round(split[2], 4)},
+                    "batched_views_per_s": round(len(w.cameras) * 1000.0 / ms_batch, 1),
+                    "cache_build_ms": round(cache_ms, 4),
+                    "duplicates_last_view": int(r.counts()[1]),
+                    "paper_fps_6dgs": paper_fps})
+        del r, rb, imgs, img_b, graph, params
+        torch.cuda.empty_cache()
+    return {"frames_per_scene": views, "l2": "flushed before each timed replay of the frames",
+            "paper_hardware": "not named in the paper", "scenes": out}
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
 
 def launches_per_frame(plan, n_cams):
     """Kernels of ours one fwd+bwd frame launches: camera upload (one per 48
@@ -449,6 +595,10 @@ def run_ours(args, world, rank, local):
                 "pairs_evaluated": n_eval, "pairs_compositing": n_comp, "warp_entries": n_warp,
                 "kernel_ms": round(dom_ms, 4)}
 
+    # ---- scale / rotation extraction (densification input), HBM roofline ----
+    scale_rot = None if args.no_extras else measure_scale_rotation(params["l_raw"], flush)
+    inference = None if args.no_extras else measure_inference(flush)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -473,6 +623,8 @@ def run_ours(args, world, rank, local):
         "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "gpu_launches": launches_per_frame(r.plan, V) * args.steps,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "scale_rotation": scale_rot,
+        "inference": inference,
         "loss": loss_batched,
     }
     if rank == 0:

@@ -90,7 +90,19 @@ typedef struct sixdgs_camera {
  *  sh   (deg+1)^2*3 planes  SH coefficient beta_{k,c} in plane k*3+c, real
  *                           orthonormal basis index k = l*l + l + m, no
  *                           Condon-Shortley phase; colour = sigmoid(sum_k
- *                           beta_k Y_k(d)) (section 4.2)                    */
+ *                           beta_k Y_k(d)) (section 4.2)
+ *  lambda_raw     1 plane   optional (NULL: settings.lambda_opa for all):
+ *                           per-Gaussian learnable lambda_opa = sigmoid(raw),
+ *                           in (0, 1) (section 4.2, Eq. pdfv2)
+ *  cond_cache    25 planes  optional (NULL: computed from l_raw and
+ *                           opacity_logit): the view-independent state written
+ *                           by sixdgs_condition_cache for these l_raw and
+ *                           opacity_logit; the projection then reads it and
+ *                           ignores l_raw and opacity_logit.  The result is
+ *                           bit-identical to the uncached projection.  For a
+ *                           fixed scene (inference; the caption of Algorithm 1)
+ *                           the state is computed once instead of every frame.
+ *                           The backward never reads it.                    */
 typedef struct sixdgs_scene {
   int64_t n;
   int32_t sh_degree;   /* 0..3 */
@@ -100,6 +112,8 @@ typedef struct sixdgs_scene {
   const float* l_raw;
   const float* opacity_logit;
   const float* sh;
+  const float* lambda_raw;
+  const float* cond_cache;
 } sixdgs_scene;
 
 /* Render settings. */
@@ -125,7 +139,10 @@ typedef struct sixdgs_settings {
   int32_t persistent;  /* 1: the blend kernels run as one resident grid whose
                           CTAs take the tiles of all cameras from a device
                           queue; 0: one CTA per tile                          */
-  int32_t _pad;
+  int32_t inference;   /* 1: forward-only plan: no gradient-record section in
+                          the workspace, the projection writes no gradient
+                          records, store_aux must be 0 and the backward entry
+                          points return SIXDGS_ERR_INVALID_ARG                */
 } sixdgs_settings;
 
 /* Sizes and workspace layout of one frame, filled by sixdgs_plan_init. */
@@ -238,6 +255,8 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* plan, void* ws_dev, size_t ws
  * images_dev: the forward output; grad_images_dev: dL/dC, same layout.
  * grad_*: outputs with the layout of the scene planes; overwritten with the
  * sum over all cameras of the plan, or added to when accumulate != 0.
+ * grad_lambda_raw is used only when the scene has a lambda_raw plane (may be
+ * NULL otherwise, or to skip that gradient).
  * The per-pair gradient records that this call accumulates are zeroed by
  * condition_project, so call it at most once per condition_project.
  * Errors: INVALID_ARG, WORKSPACE, CUDA. */
@@ -245,8 +264,8 @@ sixdgs_status sixdgs_raster_bwd(const sixdgs_plan* plan, const sixdgs_scene* sce
                                 void* ws_dev, size_t ws_bytes,
                                 const float* images_dev, const float* grad_images_dev,
                                 float* grad_mu_p, float* grad_mu_d, float* grad_l_raw,
-                                float* grad_opacity_logit, float* grad_sh, int32_t accumulate,
-                                int32_t* status_dev, sixdgs_stream_t stream);
+                                float* grad_opacity_logit, float* grad_sh, float* grad_lambda_raw,
+                                int32_t accumulate, int32_t* status_dev, sixdgs_stream_t stream);
 
 /* Stage 4a -- blend backward only (section 4.4, the differentiable 3DGS
  * rasteriser): for every (view, Gaussian) pair, the gradient of
@@ -265,8 +284,54 @@ sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* plan, void* ws_dev, size_t ws_
 sixdgs_status sixdgs_project_bwd(const sixdgs_plan* plan, const sixdgs_scene* scene,
                                  void* ws_dev, size_t ws_bytes, float* grad_mu_p,
                                  float* grad_mu_d, float* grad_l_raw, float* grad_opacity_logit,
-                                 float* grad_sh, int32_t accumulate, int32_t* status_dev,
-                                 sixdgs_stream_t stream);
+                                 float* grad_sh, float* grad_lambda_raw, int32_t accumulate,
+                                 int32_t* status_dev, sixdgs_stream_t stream);
+
+/* A whole frame in one call, for every camera of the plan: the batched
+ * driver over the stages above (condition_project, bin_sort, raster_fwd and,
+ * with targets, raster_bwd), all enqueued on `stream` so that the call can
+ * be captured as one CUDA graph.
+ * targets_dev == NULL: forward only (images_dev written; grad_images_dev,
+ *   loss_dev and every grad_* are ignored and may be NULL; the plan may be an
+ *   inference plan).
+ * targets_dev != NULL: forward with the fused L1 loss, then the backward of
+ *   that loss: *loss_dev (a double) is overwritten with the loss,
+ *   grad_images_dev receives dL/dC, grad_* are overwritten as in
+ *   sixdgs_raster_bwd (grad_lambda_raw as there).
+ * Errors: those of the stages; a capacity overflow is reported through
+ * *status_dev by bin_sort as usual. */
+sixdgs_status sixdgs_render_batched(const sixdgs_plan* plan, const sixdgs_scene* scene,
+                                    const sixdgs_camera* cams_host, void* ws_dev, size_t ws_bytes,
+                                    float* images_dev, const float* targets_dev, float* grad_images_dev,
+                                    double* loss_dev, float* grad_mu_p, float* grad_mu_d,
+                                    float* grad_l_raw, float* grad_opacity_logit, float* grad_sh,
+                                    float* grad_lambda_raw, int32_t* status_dev, sixdgs_stream_t stream);
+
+/* View-independent part of the slice (section 3.2, Eq. sigma; Algorithm 1
+ * steps 1-3) for every Gaussian, stored for the cond_cache field of
+ * sixdgs_scene: A = Sigma_pd Sigma_d^-1 (planes 0-8, row-major), the upper
+ * triangle of Sigma_d^-1 (planes 9-14: 00 01 02 11 12 22), Sigma_cond
+ * (planes 15-23, row-major) and alpha = sigmoid(opacity_logit) (plane 24;
+ * NaN for a Gaussian whose Sigma_d is not numerically positive definite,
+ * which the projection then reports as SIXDGS_ERR_NONFINITE).
+ * l_raw_dev: 21 planes, opacity_logit_dev: 1 plane, cache_dev:
+ * SIXDGS_COND_CACHE_PLANES planes, all of n floats, device memory owned by
+ * the caller.  No workspace.  Errors: INVALID_ARG, CUDA. */
+#define SIXDGS_COND_CACHE_PLANES 25
+sixdgs_status sixdgs_condition_cache(int64_t n, const float* l_raw_dev, const float* opacity_logit_dev,
+                                     float* cache_dev, sixdgs_stream_t stream);
+
+/* Scale and rotation of every conditional 3D Gaussian (section 4.3;
+ * Algorithm 1 steps 4-5), the input of adaptive density control:
+ * Sigma_cond = U D U^T, R = U with its third column multiplied by
+ * sign(det R), S = sqrt(diag D), eigenvalues in decreasing order.
+ * l_raw_dev: the scene's 21 raw Cholesky planes (n each).
+ * rotation_dev: output, 9 planes (R row-major: plane i*3+j holds R_ij);
+ * scale_dev: output, 3 planes.  No workspace.  A Gaussian whose covariance is
+ * not finite gets zeros and SIXDGS_ERR_NONFINITE in *status_dev.
+ * Errors: INVALID_ARG, CUDA. */
+sixdgs_status sixdgs_scale_rotation(int64_t n, const float* l_raw_dev, float* rotation_dev,
+                                    float* scale_dev, int32_t* status_dev, sixdgs_stream_t stream);
 
 /* Forward render without any caller-provided workspace.  The paper has no
  * counterpart: this is a convenience of this library.

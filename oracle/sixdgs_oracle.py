@@ -26,7 +26,7 @@ Definition followed, stage by stage:
   frustum guard on the Jacobian, near plane 0.2) are named constants below.
 * Loss -- section 4.4 keeps the 3DGS losses; the L1 term is used here.
 
-Readings where the paper is silent or garbled (each is listed in the design doc):
+Readings where the paper is silent or garbled:
 view direction d = normalize(mu_p - campos) per Gaussian (used for both the
 slice and the SH colour); f_cond = exp(-lambda * D) without a factor 1/2, as
 printed; mu_d is used unnormalised; opacity alpha = sigmoid(logit); real
@@ -111,6 +111,56 @@ def condition(S: torch.Tensor):
     A = S_pd @ S_d_inv
     S_cond = S_p - A @ S_pd.transpose(1, 2)
     return A, S_d_inv, S_cond
+
+
+def symmetric_eigen(S: torch.Tensor, tol=1e-15, max_sweeps=50):
+    """Eigenvalues (n, 3) and orthonormal eigenvectors (columns, n x 3 x 3) of
+    symmetric 3x3 matrices by the cyclic Jacobi method (Golub and Van Loan,
+    "Matrix Computations", section 8.5): each rotation J in the (p, q) plane
+    is chosen so that (J^T A J)_pq = 0; sweeps over the pairs (0,1), (0,2),
+    (1,2) repeat until the off-diagonal mass is below tol times the norm.
+    No LAPACK: the result is checked against a library decomposition by the
+    tests."""
+    A = S.clone()
+    n = A.shape[0]
+    V = torch.eye(3, dtype=A.dtype).repeat(n, 1, 1)
+    scale = torch.linalg.matrix_norm(A).clamp_min(1e-300)
+    for _ in range(max_sweeps):
+        off = A[:, 0, 1] ** 2 + A[:, 0, 2] ** 2 + A[:, 1, 2] ** 2
+        if bool(torch.all(off.sqrt() <= tol * scale)):
+            break
+        for p, q in ((0, 1), (0, 2), (1, 2)):
+            apq = A[:, p, q]
+            live = apq.abs() > 1e-300
+            theta = (A[:, q, q] - A[:, p, p]) / torch.where(live, 2.0 * apq, torch.ones_like(apq))
+            sgn = torch.where(theta >= 0, 1.0, -1.0).to(A.dtype)
+            t = torch.where(live, sgn / (theta.abs() + torch.sqrt(theta * theta + 1.0)), torch.zeros_like(apq))
+            c = 1.0 / torch.sqrt(t * t + 1.0)
+            s_ = t * c
+            J = torch.eye(3, dtype=A.dtype).repeat(n, 1, 1)
+            J[:, p, p] = c
+            J[:, q, q] = c
+            J[:, p, q] = s_
+            J[:, q, p] = -s_
+            A = J.transpose(1, 2) @ A @ J
+            V = V @ J
+    return torch.diagonal(A, dim1=1, dim2=2), V
+
+
+def scale_rotation(S_cond: torch.Tensor):
+    """Rotation R (n, 3, 3) and scale S (n, 3) of the conditional Gaussian
+    (section 4.3; Algorithm 1 steps 4-5): Sigma_cond = U D U^T, R = U,
+    S = sqrt(diag D), then the third column of R multiplied by sign(det R).
+    Sigma_cond is symmetric positive definite, so its singular value
+    decomposition is its eigen-decomposition with the eigenvalues in
+    decreasing order (the order a singular value decomposition returns)."""
+    w, U = symmetric_eigen(S_cond)
+    order = torch.argsort(w, dim=1, descending=True)
+    D = torch.gather(w, 1, order)
+    R = torch.gather(U, 2, order[:, None, :].expand(-1, 3, -1)).clone()
+    sign = torch.sign(torch.linalg.det(R))
+    R[:, :, 2] = R[:, :, 2] * sign[:, None]
+    return R, torch.sqrt(D)
 
 
 # ==========================================================================
@@ -275,8 +325,11 @@ def prepare_view(p, sh_degree, cam, settings: Settings) -> ViewPrep:
     L = cholesky_factor(p["l_raw"])
     A, S_d_inv, S_cond = condition(covariance(L))
     alpha = torch.sigmoid(p["opacity_logit"])
+    # lambda_opa: the global hyper-parameter, or per Gaussian (section 4.2),
+    # parametrised as sigmoid(raw) so that 0 < lambda_opa < 1
+    lam = torch.sigmoid(p["lambda_raw"]) if "lambda_raw" in p else settings.lambda_opa
     d = view_direction(mu_p, cam.campos)
-    mu_cond, D, alpha_cond = slice_at(mu_p, mu_d, A, S_d_inv, alpha, d, settings.lambda_opa)
+    mu_cond, D, alpha_cond = slice_at(mu_p, mu_d, A, S_d_inv, alpha, d, lam)
     rgb = sh_colour(p["sh"], d, sh_degree)
     t, mean2d, cov2d, det, conic, radius = project(mu_cond, S_cond, cam)
     rect = tile_rect(mean2d.detach(), radius.detach(), cam, settings.tile_w, settings.tile_h)

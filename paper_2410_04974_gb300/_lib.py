@@ -24,14 +24,15 @@ class Camera(ctypes.Structure):
 
 class Scene(ctypes.Structure):
     _fields_ = [("n", c_int64), ("sh_degree", c_int32), ("_pad", c_int32), ("mu_p", c_void_p),
-                ("mu_d", c_void_p), ("l_raw", c_void_p), ("opacity_logit", c_void_p), ("sh", c_void_p)]
+                ("mu_d", c_void_p), ("l_raw", c_void_p), ("opacity_logit", c_void_p), ("sh", c_void_p),
+                ("lambda_raw", c_void_p), ("cond_cache", c_void_p)]
 
 
 class Settings(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("lambda_opa", c_float),
                 ("bg", c_float * 3), ("store_aux", c_int32), ("spin_budget", c_int64),
                 ("loss_norm", c_float), ("count_pairs", c_int32), ("persistent", c_int32),
-                ("_pad", c_int32)]
+                ("inference", c_int32)]
 
 
 class Plan(ctypes.Structure):
@@ -54,16 +55,21 @@ EXPORTS = {
                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "sixdgs_raster_bwd": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), c_void_p, c_size_t,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                    c_void_p, c_int32, c_void_p, c_void_p]),
+                                    c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sixdgs_blend_bwd": (c_int32, [ctypes.POINTER(Plan), c_void_p, c_size_t, c_void_p, c_void_p,
                                    c_void_p, c_void_p]),
+    "sixdgs_render_batched": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), ctypes.POINTER(Camera),
+                                        c_void_p, c_size_t] + [c_void_p] * 12),
+    "sixdgs_condition_cache": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sixdgs_scale_rotation": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sixdgs_render_fwd_static": (c_int32, [c_int64, c_int32, ctypes.POINTER(Scene), ctypes.POINTER(Camera),
                                            c_int32, ctypes.POINTER(Settings), c_void_p, c_void_p, c_void_p]),
     "sixdgs_project_bwd": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), c_void_p, c_size_t,
-                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                      c_void_p, c_void_p]),
 }
 
+COND_CACHE_PLANES = 25
 STATIC_WS_BYTES = 32 << 20   # SIXDGS_STATIC_WS_BYTES
 
 _LIB = None

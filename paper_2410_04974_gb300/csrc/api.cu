@@ -106,6 +106,12 @@ bool valid_scene(const sixdgs_plan* p, const sixdgs_scene* s) {
          (p->n == 0 || (s->mu_p && s->mu_d && s->l_raw && s->opacity_logit && s->sh));
 }
 
+// The projection needs l_raw and opacity_logit only without a cached state.
+bool valid_fwd_scene(const sixdgs_plan* p, const sixdgs_scene* s) {
+  return s && s->n == p->n && s->sh_degree == p->sh_degree &&
+         (p->n == 0 || (s->mu_p && s->mu_d && s->sh && (s->cond_cache || (s->l_raw && s->opacity_logit))));
+}
+
 }  // namespace
 
 extern "C" {
@@ -134,6 +140,8 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   if (!(st->tile_h == 8 || st->tile_h == 16)) return SIXDGS_ERR_INVALID_ARG;
   if (st->batch < 32 || st->batch > 1024 || st->batch % 32) return SIXDGS_ERR_INVALID_ARG;
   if (!(st->lambda_opa >= 0.f) || !(st->lambda_opa <= 1.f)) return SIXDGS_ERR_INVALID_ARG;
+  if (st->inference != 0 && st->inference != 1) return SIXDGS_ERR_INVALID_ARG;
+  if (st->inference && st->store_aux) return SIXDGS_ERR_INVALID_ARG;
   const int64_t n_pairs = (int64_t)n_cams * n;
   if (n_pairs >= ((int64_t)1 << 31)) return SIXDGS_ERR_INVALID_ARG;
   std::memset(plan, 0, sizeof(*plan));
@@ -178,7 +186,7 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   take(SIXDGS_WS_NTILES, np4 * 4);
   take(SIXDGS_WS_RECT, n_pairs * 8);
   take(SIXDGS_WS_DEPTHKEY, n_pairs * 4);
-  take(SIXDGS_WS_GRADREC, n_pairs * 48);
+  take(SIXDGS_WS_GRADREC, st->inference ? 0 : n_pairs * 48);
   take(SIXDGS_WS_RANGES, tiles * 8);
   take(SIXDGS_WS_NWALK, st->store_aux ? pixels * 4 : 0);
   // cleared at the start of every bin_sort
@@ -213,7 +221,7 @@ sixdgs_status sixdgs_condition_project(const sixdgs_plan* p, const sixdgs_scene*
                                        int32_t* status_dev, sixdgs_stream_t stream_) {
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
-  if (!valid_scene(p, scene) || !cams) return SIXDGS_ERR_INVALID_ARG;
+  if (!valid_fwd_scene(p, scene) || !cams) return SIXDGS_ERR_INVALID_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   CamRec* dcams = ws_ptr<CamRec>(ws, p, SIXDGS_WS_CAMS);
   int32_t tile_offset = 0;
@@ -244,11 +252,13 @@ sixdgs_status sixdgs_condition_project(const sixdgs_plan* p, const sixdgs_scene*
   a.l_raw = scene->l_raw;
   a.opacity_logit = scene->opacity_logit;
   a.sh = scene->sh;
+  a.lambda_raw = scene->lambda_raw;
+  a.cond_cache = scene->cond_cache;
   a.rec = ws_ptr<PairRec>(ws, p, SIXDGS_WS_REC);
   a.ntiles = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_NTILES);
   a.rect = ws_ptr<ushort4>(ws, p, SIXDGS_WS_RECT);
   a.depth_key = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_DEPTHKEY);
-  a.grad_rec = ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
+  a.grad_rec = p->settings.inference ? nullptr : ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
   a.status = status_dev;
   launch_project_fwd(a, stream);
   return launch_status();
@@ -417,6 +427,7 @@ sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, 
                                const float* grad_images_dev, int32_t* status_dev, sixdgs_stream_t stream_) {
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
+  if (p->settings.inference) return SIXDGS_ERR_INVALID_ARG;
   if (!images_dev || !grad_images_dev) return SIXDGS_ERR_INVALID_ARG;
   BlendArgs a = blend_args(p, ws);
   a.images_in = images_dev;
@@ -430,11 +441,12 @@ sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, 
 
 sixdgs_status sixdgs_project_bwd(const sixdgs_plan* p, const sixdgs_scene* scene, void* ws,
                                  size_t ws_bytes, float* grad_mu_p, float* grad_mu_d, float* grad_l_raw,
-                                 float* grad_opacity_logit, float* grad_sh, int32_t accumulate,
-                                 int32_t* status_dev, sixdgs_stream_t stream_) {
+                                 float* grad_opacity_logit, float* grad_sh, float* grad_lambda_raw,
+                                 int32_t accumulate, int32_t* status_dev, sixdgs_stream_t stream_) {
   (void)status_dev;
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
+  if (p->settings.inference) return SIXDGS_ERR_INVALID_ARG;
   if (!valid_scene(p, scene)) return SIXDGS_ERR_INVALID_ARG;
   if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
     return SIXDGS_ERR_INVALID_ARG;
@@ -450,6 +462,7 @@ sixdgs_status sixdgs_project_bwd(const sixdgs_plan* p, const sixdgs_scene* scene
   b.l_raw = scene->l_raw;
   b.opacity_logit = scene->opacity_logit;
   b.sh = scene->sh;
+  b.lambda_raw = scene->lambda_raw;
   b.rec = ws_ptr<PairRec>(ws, p, SIXDGS_WS_REC);
   b.ntiles = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_NTILES);
   b.grad_rec = ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
@@ -458,6 +471,7 @@ sixdgs_status sixdgs_project_bwd(const sixdgs_plan* p, const sixdgs_scene* scene
   b.grad_l_raw = grad_l_raw;
   b.grad_opacity_logit = grad_opacity_logit;
   b.grad_sh = grad_sh;
+  b.grad_lambda_raw = grad_lambda_raw;
   b.accumulate = accumulate;
   launch_sh_bwd(b, stream);
   launch_geom_bwd(b, stream);
@@ -468,16 +482,71 @@ sixdgs_status sixdgs_raster_bwd(const sixdgs_plan* p, const sixdgs_scene* scene,
                                 size_t ws_bytes, const float* images_dev,
                                 const float* grad_images_dev, float* grad_mu_p, float* grad_mu_d,
                                 float* grad_l_raw, float* grad_opacity_logit, float* grad_sh,
-                                int32_t accumulate, int32_t* status_dev, sixdgs_stream_t stream) {
+                                float* grad_lambda_raw, int32_t accumulate, int32_t* status_dev,
+                                sixdgs_stream_t stream) {
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
+  if (p->settings.inference) return SIXDGS_ERR_INVALID_ARG;
   if (!valid_scene(p, scene)) return SIXDGS_ERR_INVALID_ARG;
   if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
     return SIXDGS_ERR_INVALID_ARG;
   e = sixdgs_blend_bwd(p, ws, ws_bytes, images_dev, grad_images_dev, status_dev, stream);
   if (e != SIXDGS_OK) return e;
   return sixdgs_project_bwd(p, scene, ws, ws_bytes, grad_mu_p, grad_mu_d, grad_l_raw, grad_opacity_logit,
-                            grad_sh, accumulate, status_dev, stream);
+                            grad_sh, grad_lambda_raw, accumulate, status_dev, stream);
+}
+
+sixdgs_status sixdgs_render_batched(const sixdgs_plan* p, const sixdgs_scene* scene,
+                                    const sixdgs_camera* cams_host, void* ws, size_t ws_bytes,
+                                    float* images_dev, const float* targets_dev, float* grad_images_dev,
+                                    double* loss_dev, float* grad_mu_p, float* grad_mu_d, float* grad_l_raw,
+                                    float* grad_opacity_logit, float* grad_sh, float* grad_lambda_raw,
+                                    int32_t* status_dev, sixdgs_stream_t stream) {
+  sixdgs_status e = check_ws(p, ws, ws_bytes);
+  if (e != SIXDGS_OK) return e;
+  const bool train = targets_dev != nullptr;
+  if (train) {
+    if (p->settings.inference || !grad_images_dev || !loss_dev || !valid_scene(p, scene))
+      return SIXDGS_ERR_INVALID_ARG;
+    if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
+      return SIXDGS_ERR_INVALID_ARG;
+    if (cudaMemsetAsync(loss_dev, 0, sizeof(double), reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+      return SIXDGS_ERR_CUDA;
+  }
+  e = sixdgs_condition_project(p, scene, cams_host, ws, ws_bytes, status_dev, stream);
+  if (e != SIXDGS_OK) return e;
+  e = sixdgs_bin_sort(p, ws, ws_bytes, status_dev, stream);
+  if (e != SIXDGS_OK) return e;
+  e = sixdgs_raster_fwd(p, ws, ws_bytes, images_dev, targets_dev, train ? grad_images_dev : nullptr,
+                        train ? loss_dev : nullptr, status_dev, stream);
+  if (e != SIXDGS_OK || !train) return e;
+  return sixdgs_raster_bwd(p, scene, ws, ws_bytes, images_dev, grad_images_dev, grad_mu_p, grad_mu_d,
+                           grad_l_raw, grad_opacity_logit, grad_sh, grad_lambda_raw, 0, status_dev, stream);
+}
+
+sixdgs_status sixdgs_condition_cache(int64_t n, const float* l_raw_dev, const float* opacity_logit_dev,
+                                     float* cache_dev, sixdgs_stream_t stream) {
+  if (n < 0 || (n > 0 && (!l_raw_dev || !opacity_logit_dev || !cache_dev))) return SIXDGS_ERR_INVALID_ARG;
+  CondCacheArgs a;
+  a.n = n;
+  a.l_raw = l_raw_dev;
+  a.opacity_logit = opacity_logit_dev;
+  a.cache = cache_dev;
+  launch_cond_cache(a, reinterpret_cast<cudaStream_t>(stream));
+  return launch_status();
+}
+
+sixdgs_status sixdgs_scale_rotation(int64_t n, const float* l_raw_dev, float* rotation_dev, float* scale_dev,
+                                    int32_t* status_dev, sixdgs_stream_t stream) {
+  if (n < 0 || (n > 0 && (!l_raw_dev || !rotation_dev || !scale_dev))) return SIXDGS_ERR_INVALID_ARG;
+  ScaleRotationArgs a;
+  a.n = n;
+  a.l_raw = l_raw_dev;
+  a.rotation = rotation_dev;
+  a.scale = scale_dev;
+  a.status = status_dev;
+  launch_scale_rotation(a, reinterpret_cast<cudaStream_t>(stream));
+  return launch_status();
 }
 
 }  // extern "C"

@@ -30,7 +30,11 @@ __device__ __forceinline__ void load_cholesky(const float* __restrict__ l_raw, i
   for (int i = 1; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < i; ++j) {
-      L[i][j] = 2.f * sigmoidf_(__ldg(l_raw + (k++) * n + g)) - 1.f;
+      // 2 sigmoid(x) - 1, evaluated as the identical function tanh(x / 2):
+      // the subtraction form loses the relative accuracy of small entries
+      // (|v| ~ 1e-3 keeps only ~3 significant digits in FP32), tanhf keeps
+      // it to a few ulps.
+      L[i][j] = tanhf(0.5f * __ldg(l_raw + (k++) * n + g));
     }
 }
 

@@ -17,11 +17,13 @@ struct ProjectArgs {
   const float* l_raw;
   const float* opacity_logit;
   const float* sh;
+  const float* lambda_raw;   // optional per-Gaussian lambda_opa (pre-sigmoid)
+  const float* cond_cache;   // optional cached view-independent state
   PairRec* rec;
   uint32_t* ntiles;
   ushort4* rect;
   uint32_t* depth_key;
-  float* grad_rec;   // zeroed for every visible pair (read by the backward)
+  float* grad_rec;   // zeroed for every visible pair (read by the backward); null: inference plan
   int32_t* status;
 };
 
@@ -125,6 +127,7 @@ struct ProjectBwdArgs {
   const float* l_raw;
   const float* opacity_logit;
   const float* sh;
+  const float* lambda_raw;
   const PairRec* rec;
   const uint32_t* ntiles;
   const float* grad_rec;
@@ -133,10 +136,30 @@ struct ProjectBwdArgs {
   float* grad_l_raw;
   float* grad_opacity_logit;
   float* grad_sh;
+  float* grad_lambda_raw;
   int32_t accumulate;   // 1: add into the outputs instead of overwriting
 };
 
+struct CondCacheArgs {
+  int64_t n;
+  const float* l_raw;
+  const float* opacity_logit;
+  float* cache;      // kCondCachePlanes planes of n floats
+};
+
+constexpr int kCondCachePlanes = 25;
+
+struct ScaleRotationArgs {
+  int64_t n;
+  const float* l_raw;
+  float* rotation;   // 9 planes, R row-major
+  float* scale;      // 3 planes
+  int32_t* status;
+};
+
 void launch_project_fwd(const ProjectArgs& a, cudaStream_t stream);
+void launch_scale_rotation(const ScaleRotationArgs& a, cudaStream_t stream);
+void launch_cond_cache(const CondCacheArgs& a, cudaStream_t stream);
 void launch_compact(const CompactArgs& a, int grid, cudaStream_t stream);
 void launch_onesweep(const OnesweepArgs& a, int grid, cudaStream_t stream);
 void launch_emit(const EmitArgs& a, int grid, cudaStream_t stream);

@@ -7,6 +7,12 @@
 // computed once in registers and reused for every camera, so the 304 bytes
 // of parameters of a Gaussian are read from HBM once per frame however many
 // cameras there are.  Loads are coalesced structure-of-arrays planes.
+//
+// Inference (the Algorithm 1 caption: the view-independent terms are
+// computed once when the scene is fixed): cond_cache_kernel stores that
+// state once, and the cached variant of the projection loads it instead of
+// recomputing it; every later step is the same code on the same values, so
+// the two variants give bit-identical records.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "cond.cuh"
@@ -15,6 +21,46 @@
 
 namespace sixdgs {
 
+// Cached view-independent state (written by cond_cache_kernel): plane k of
+// A (k < 9), the upper triangle of the symmetric Sigma_d^-1 (9..14), plane k
+// of Sigma_cond (15..23) and alpha (24; NaN where Sigma_d was not
+// numerically positive definite).
+__device__ __forceinline__ void load_cond_cache(const float* __restrict__ c, int64_t n, int64_t g,
+                                                CondState& cs) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) cs.A.m[k] = __ldg(c + k * n + g);
+  cs.Sdi(0, 0) = __ldg(c + 9 * n + g);
+  cs.Sdi(0, 1) = cs.Sdi(1, 0) = __ldg(c + 10 * n + g);
+  cs.Sdi(0, 2) = cs.Sdi(2, 0) = __ldg(c + 11 * n + g);
+  cs.Sdi(1, 1) = __ldg(c + 12 * n + g);
+  cs.Sdi(1, 2) = cs.Sdi(2, 1) = __ldg(c + 13 * n + g);
+  cs.Sdi(2, 2) = __ldg(c + 14 * n + g);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) cs.Sc.m[k] = __ldg(c + (15 + k) * n + g);
+  cs.alpha = __ldg(c + 24 * n + g);
+}
+
+__global__ void __launch_bounds__(128) cond_cache_kernel(CondCacheArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n) return;
+  const int64_t n = a.n;
+  CondState cs;
+  const bool ok = condition_gaussian(a.l_raw, __ldg(a.opacity_logit + g), n, g, cs);
+  float* c = a.cache;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c[k * n + g] = cs.A.m[k];
+  c[9 * n + g] = cs.Sdi(0, 0);
+  c[10 * n + g] = cs.Sdi(0, 1);
+  c[11 * n + g] = cs.Sdi(0, 2);
+  c[12 * n + g] = cs.Sdi(1, 1);
+  c[13 * n + g] = cs.Sdi(1, 2);
+  c[14 * n + g] = cs.Sdi(2, 2);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c[(15 + k) * n + g] = cs.Sc.m[k];
+  c[24 * n + g] = ok ? cs.alpha : __int_as_float(0x7fc00000);
+}
+
+template <bool kCached>
 __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
   extern __shared__ CamRec s_cams[];
   for (int i = threadIdx.x; i < a.n_cams; i += blockDim.x) s_cams[i] = a.cams[i];
@@ -30,7 +76,13 @@ __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
     md[i] = __ldg(a.mu_d + i * n + g);
   }
   CondState cs;
-  bool ok = condition_gaussian(a.l_raw, __ldg(a.opacity_logit + g), n, g, cs);
+  bool ok = true;
+  if constexpr (kCached)
+    load_cond_cache(a.cond_cache, n, g, cs);
+  else
+    ok = condition_gaussian(a.l_raw, __ldg(a.opacity_logit + g), n, g, cs);
+  // lambda_opa: global, or per Gaussian as sigmoid(raw) (section 4.2)
+  const float lam = a.lambda_raw ? sigmoidf_(__ldg(a.lambda_raw + g)) : a.lambda_opa;
   const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
   float beta[kMaxShCoeffs][3];
 #pragma unroll
@@ -42,7 +94,7 @@ __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
     for (int k = 0; k < 9; ++k)
       ok = ok && isfinite(cs.A.m[k]) && isfinite(cs.Sdi.m[k]) && isfinite(cs.Sc.m[k]);
     ok = ok && isfinite(mp[0]) && isfinite(mp[1]) && isfinite(mp[2]) && isfinite(md[0]) &&
-         isfinite(md[1]) && isfinite(md[2]) && isfinite(cs.alpha);
+         isfinite(md[1]) && isfinite(md[2]) && isfinite(cs.alpha) && isfinite(lam);
   }
   if (!ok) raise_status(a.status, SIXDGS_ERR_NONFINITE);
 
@@ -61,7 +113,7 @@ __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
       mat_vec(cs.Sdi, delta, Sd_delta);
       float mc[3] = {mp[0] + Ad[0], mp[1] + Ad[1], mp[2] + Ad[2]};
       float D = delta[0] * Sd_delta[0] + delta[1] * Sd_delta[1] + delta[2] * Sd_delta[2];
-      float alpha_cond = cs.alpha * __expf(-a.lambda_opa * D);
+      float alpha_cond = cs.alpha * __expf(-lam * D);
       // ---- projection (section 4.4, EWA) ----
       float t[3];
 #pragma unroll
@@ -137,8 +189,10 @@ __global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
             rec.b = make_float4(-0.5f * kLog2e * con_c, lo, rgb[0], rgb[1]);
             rec.c = make_float4(rgb[2], hx, hy, t[2]);
             a.rec[pair] = rec;
-            float4* gr = reinterpret_cast<float4*>(a.grad_rec) + pair * 3;
-            gr[0] = gr[1] = gr[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.grad_rec) {
+              float4* gr = reinterpret_cast<float4*>(a.grad_rec) + pair * 3;
+              gr[0] = gr[1] = gr[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             a.depth_key[pair] = __float_as_uint(t[2]);
             a.rect[pair] = make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0,
                                         (unsigned short)y1);
@@ -155,7 +209,15 @@ void launch_project_fwd(const ProjectArgs& a, cudaStream_t stream) {
   const int threads = 128;
   const int64_t blocks = (a.n + threads - 1) / threads;
   size_t smem = sizeof(CamRec) * (size_t)a.n_cams;
-  project_fwd_kernel<<<(unsigned)blocks, threads, smem, stream>>>(a);
+  if (a.cond_cache)
+    project_fwd_kernel<true><<<(unsigned)blocks, threads, smem, stream>>>(a);
+  else
+    project_fwd_kernel<false><<<(unsigned)blocks, threads, smem, stream>>>(a);
+}
+
+void launch_cond_cache(const CondCacheArgs& a, cudaStream_t stream) {
+  if (a.n == 0) return;
+  cond_cache_kernel<<<(unsigned)((a.n + 127) / 128), 128, 0, stream>>>(a);
 }
 
 }  // namespace sixdgs

@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
   const M3 A = mul(P, S);
   const M3 Sc = sub(Sp, mul_bt(A, P));
   const float alpha = sigmoidf_(__ldg(a.opacity_logit + g));
+  const float lam = a.lambda_raw ? sigmoidf_(__ldg(a.lambda_raw + g)) : a.lambda_opa;
 
   M3 gA = zero3(), gS = zero3(), gSc = zero3();
-  float gmp[3] = {0.f, 0.f, 0.f}, gmd[3] = {0.f, 0.f, 0.f}, galpha = 0.f;
+  float gmp[3] = {0.f, 0.f, 0.f}, gmd[3] = {0.f, 0.f, 0.f}, galpha = 0.f, glam = 0.f;
   const float4* grec = reinterpret_cast<const float4*>(a.grad_rec);
 
   for (int v = 0; v < a.n_cams && ok; ++v) {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
     mat_vec(S, delta, Sdl);
     const float mc[3] = {mp[0] + Ad[0], mp[1] + Ad[1], mp[2] + Ad[2]};
     const float D = delta[0] * Sdl[0] + delta[1] * Sdl[1] + delta[2] * Sdl[2];
-    const float f = __expf(-a.lambda_opa * D);
+    const float f = __expf(-lam * D);
     const float alpha_cond = alpha * f;
     float t[3];
 #pragma unroll
@@ -224,8 +225,9 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
     // ---- slice backward (Eq. mu, Eq. pdfv2, Eq. alpha) ----
     float ddelta[3];
     mat_t_vec(A, dmc, ddelta);
-    const float dD = -a.lambda_opa * alpha_cond * dalpha_cond;
+    const float dD = -lam * alpha_cond * dalpha_cond;
     galpha += f * dalpha_cond;
+    glam -= D * alpha_cond * dalpha_cond;   // d alpha_cond / d lambda = -D alpha_cond
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       gmp[i] += dmc[i];
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) dL[i][j] = 0.f;
     galpha = 0.f;
+    glam = 0.f;
   }
   const bool acc = a.accumulate != 0;
 #pragma unroll
@@ -306,6 +309,10 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
     }
   const float gl = galpha * alpha * (1.f - alpha);
   a.grad_opacity_logit[g] = acc ? a.grad_opacity_logit[g] + gl : gl;
+  if (a.lambda_raw && a.grad_lambda_raw) {
+    const float gr = glam * lam * (1.f - lam);
+    a.grad_lambda_raw[g] = acc ? a.grad_lambda_raw[g] + gr : gr;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     a.grad_mu_d[i * n + g] = acc ? a.grad_mu_d[i * n + g] + gmd[i] : gmd[i];

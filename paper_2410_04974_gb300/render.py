@@ -38,7 +38,8 @@ def camera_array(cams):
 
 
 def make_settings(tile=(16, 16), batch=512, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
-                  spin_budget=0, loss_norm=0.0, count_pairs=False, persistent=False) -> _lib.Settings:
+                  spin_budget=0, loss_norm=0.0, count_pairs=False, persistent=False,
+                  inference=False) -> _lib.Settings:
     s = _lib.Settings()
     s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
     s.batch = int(batch)
@@ -50,6 +51,7 @@ def make_settings(tile=(16, 16), batch=512, lambda_opa=0.35, bg=(1.0, 1.0, 1.0),
     s.loss_norm = float(loss_norm)
     s.count_pairs = 1 if count_pairs else 0
     s.persistent = 1 if persistent else 0
+    s.inference = 1 if inference else 0
     return s
 
 
@@ -66,11 +68,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+OPTIONAL_PARAMS = ("lambda_raw",)
+
+
 def params_to_device(scene, device="cuda"):
-    """Scene planes (synth.Scene or dict of arrays) as contiguous float32 device tensors."""
+    """Scene planes (synth.Scene or dict of arrays) as contiguous float32 device
+    tensors; includes the optional per-Gaussian lambda_raw plane when present."""
     planes = scene.planes() if hasattr(scene, "planes") else scene
-    return {k: torch.as_tensor(np.asarray(planes[k], dtype=np.float32)).to(device).contiguous()
-            for k in PARAM_NAMES}
+    names = list(PARAM_NAMES) + [k for k in OPTIONAL_PARAMS if planes.get(k) is not None]
+    return {k: torch.as_tensor(np.asarray(planes[k], dtype=np.float32)).to(device).contiguous() for k in names}
 
 
 class Renderer:
@@ -82,7 +88,7 @@ class Renderer:
 
     def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=512, lambda_opa=0.35,
                  bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, loss_norm=0.0,
-                 count_pairs=False, persistent=False, device="cuda"):
+                 count_pairs=False, persistent=False, inference=False, device="cuda"):
         if not torch.cuda.is_available():
             raise _lib.SixDGSError("sixdgs needs a CUDA device; there is no CPU path")
         self.lib = _lib.load()
@@ -90,7 +96,7 @@ class Renderer:
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cameras = list(cameras)
         self.settings = make_settings(tile, batch, lambda_opa, bg, store_aux, spin_budget, loss_norm,
-                                      count_pairs, persistent)
+                                      count_pairs, persistent, inference)
         self.cams = camera_array(self.cameras)
         self._make_plan(dup_capacity)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
@@ -105,8 +111,10 @@ class Renderer:
     def scene_struct(self, params) -> _lib.Scene:
         s = _lib.Scene()
         s.n, s.sh_degree = self.n, self.sh_degree
-        for k in PARAM_NAMES:
-            t = params[k]
+        for k in PARAM_NAMES + OPTIONAL_PARAMS + ("cond_cache",):
+            t = params.get(k)
+            if t is None:
+                continue
             assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), k
             setattr(s, k, t.data_ptr())
         return s
@@ -162,7 +170,8 @@ class Renderer:
                                               _ptr(images), _ptr(grad_images), _ptr(grads["mu_p"]),
                                               _ptr(grads["mu_d"]), _ptr(grads["l_raw"]),
                                               _ptr(grads["opacity_logit"]), _ptr(grads["sh"]),
-                                              int(accumulate), _ptr(self.status), self._stream(stream)),
+                                              _ptr(grads.get("lambda_raw")), int(accumulate), _ptr(self.status),
+                                              self._stream(stream)),
                    "sixdgs_raster_bwd")
 
     def blend_bwd(self, images, grad_images, stream=None):
@@ -175,8 +184,22 @@ class Renderer:
         sc = self.scene_struct(params)
         _lib.check(self.lib.sixdgs_project_bwd(ctypes.byref(self.plan), ctypes.byref(sc), ws, nb,
                                                _ptr(grads["mu_p"]), _ptr(grads["mu_d"]), _ptr(grads["l_raw"]),
-                                               _ptr(grads["opacity_logit"]), _ptr(grads["sh"]), int(accumulate),
+                                               _ptr(grads["opacity_logit"]), _ptr(grads["sh"]),
+                                               _ptr(grads.get("lambda_raw")), int(accumulate),
                                                _ptr(self.status), self._stream(stream)), "sixdgs_project_bwd")
+
+    def step(self, params, images, targets=None, grad_images=None, grads=None, stream=None):
+        """The whole frame in one library call (sixdgs_render_batched): forward
+        only without targets, else forward + L1 loss (into self.loss) +
+        backward into `grads` (overwritten)."""
+        ws, nb = self._wsargs()
+        sc = self.scene_struct(params)
+        g = grads or {}
+        _lib.check(self.lib.sixdgs_render_batched(
+            ctypes.byref(self.plan), ctypes.byref(sc), self.cams, ws, nb, _ptr(images), _ptr(targets),
+            _ptr(grad_images), _ptr(self.loss) if targets is not None else None, _ptr(g.get("mu_p")),
+            _ptr(g.get("mu_d")), _ptr(g.get("l_raw")), _ptr(g.get("opacity_logit")), _ptr(g.get("sh")),
+            _ptr(g.get("lambda_raw")), _ptr(self.status), self._stream(stream)), "sixdgs_render_batched")
 
     def set_cameras(self, cameras):
         """Swap in cameras of the same sizes (same plan and workspace)."""
@@ -187,7 +210,7 @@ class Renderer:
         self.cams = camera_array(cameras)
 
     def new_grads(self, params):
-        return {k: torch.empty_like(params[k]) for k in PARAM_NAMES}
+        return {k: torch.empty_like(params[k]) for k in PARAM_NAMES + OPTIONAL_PARAMS if k in params}
 
     # ---- frames -----------------------------------------------------------
     def forward(self, params, targets=None, stream=None, check=True):
@@ -271,12 +294,16 @@ class Renderer:
 
 
 class RenderFunction(torch.autograd.Function):
-    """images = render(params); backward through the hand-written kernels."""
+    """images = render(params); backward through the hand-written kernels.
+    lambda_raw (per-Gaussian lambda_opa) is optional: pass None to use the
+    renderer's global lambda_opa."""
 
     @staticmethod
-    def forward(ctx, renderer: Renderer, mu_p, mu_d, l_raw, opacity_logit, sh):
+    def forward(ctx, renderer: Renderer, mu_p, mu_d, l_raw, opacity_logit, sh, lambda_raw=None):
         params = {"mu_p": mu_p.contiguous(), "mu_d": mu_d.contiguous(), "l_raw": l_raw.contiguous(),
                   "opacity_logit": opacity_logit.contiguous(), "sh": sh.contiguous()}
+        if lambda_raw is not None:
+            params["lambda_raw"] = lambda_raw.contiguous()
         images = renderer.forward(params)
         ctx.renderer = renderer
         ctx.params = params
@@ -287,9 +314,43 @@ class RenderFunction(torch.autograd.Function):
     def backward(ctx, grad_images):
         (images,) = ctx.saved_tensors
         g = ctx.renderer.backward(ctx.params, images, grad_images.contiguous())
-        return None, g["mu_p"], g["mu_d"], g["l_raw"], g["opacity_logit"], g["sh"]
+        return None, g["mu_p"], g["mu_d"], g["l_raw"], g["opacity_logit"], g["sh"], g.get("lambda_raw")
 
 
 def render(renderer: Renderer, params):
     """Differentiable render: packed images of every camera."""
-    return RenderFunction.apply(renderer, *(params[k] for k in PARAM_NAMES))
+    return RenderFunction.apply(renderer, *(params[k] for k in PARAM_NAMES), params.get("lambda_raw"))
+
+
+def scale_rotation(l_raw, stream=None):
+    """Per-Gaussian rotation (9, n) and scale (3, n) of the conditional
+    covariance (section 4.3, Algorithm 1 steps 4-5), from the (21, n) raw
+    Cholesky planes on the GPU."""
+    lib = _lib.load()
+    n = int(l_raw.shape[1])
+    assert l_raw.is_cuda and l_raw.dtype == torch.float32 and l_raw.is_contiguous()
+    rot = torch.empty((9, n), dtype=torch.float32, device=l_raw.device)
+    scale = torch.empty((3, n), dtype=torch.float32, device=l_raw.device)
+    status = torch.zeros(1, dtype=torch.int32, device=l_raw.device)
+    s = stream if stream is not None else torch.cuda.current_stream(l_raw.device)
+    _lib.check(lib.sixdgs_scale_rotation(n, _ptr(l_raw), _ptr(rot), _ptr(scale), _ptr(status),
+                                         ctypes.c_void_p(s.cuda_stream)), "sixdgs_scale_rotation")
+    return rot, scale, status
+
+
+def condition_cache(params, stream=None):
+    """View-independent slice state of every Gaussian (section 3.2, Eq. sigma;
+    Algorithm 1 steps 1-3), a (25, n) device tensor.  Put it in the params
+    dict under "cond_cache" and the forward projection reads it instead of
+    recomputing it (same result, bit for bit); recompute it whenever l_raw or
+    opacity_logit change."""
+    lib = _lib.load()
+    l_raw, logit = params["l_raw"], params["opacity_logit"]
+    n = int(l_raw.shape[1])
+    for t in (l_raw, logit):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    cache = torch.empty((_lib.COND_CACHE_PLANES, n), dtype=torch.float32, device=l_raw.device)
+    s = stream if stream is not None else torch.cuda.current_stream(l_raw.device)
+    _lib.check(lib.sixdgs_condition_cache(n, _ptr(l_raw), _ptr(logit), _ptr(cache),
+                                          ctypes.c_void_p(s.cuda_stream)), "sixdgs_condition_cache")
+    return cache

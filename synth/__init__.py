@@ -49,6 +49,7 @@ class Scene:
     opacity_logit: np.ndarray
     sh: np.ndarray
     sh_degree: int
+    lambda_raw: np.ndarray | None = None   # optional per-Gaussian pre-sigmoid lambda_opa
 
     @property
     def n(self) -> int:
@@ -58,11 +59,15 @@ class Scene:
         idx = np.asarray(idx)
         return Scene(self.mu_p[:, idx].copy(), self.mu_d[:, idx].copy(),
                      self.l_raw[:, idx].copy(), self.opacity_logit[idx].copy(),
-                     self.sh[:, idx].copy(), self.sh_degree)
+                     self.sh[:, idx].copy(), self.sh_degree,
+                     None if self.lambda_raw is None else self.lambda_raw[idx].copy())
 
     def planes(self) -> dict:
-        return {"mu_p": self.mu_p, "mu_d": self.mu_d, "l_raw": self.l_raw,
-                "opacity_logit": self.opacity_logit, "sh": self.sh}
+        out = {"mu_p": self.mu_p, "mu_d": self.mu_d, "l_raw": self.l_raw,
+               "opacity_logit": self.opacity_logit, "sh": self.sh}
+        if self.lambda_raw is not None:
+            out["lambda_raw"] = self.lambda_raw
+        return out
 
 
 @dataclasses.dataclass
@@ -240,7 +245,20 @@ def perturb(scene: Scene, seed: int) -> Scene:
         f32(scene.l_raw + rng.normal(0.0, 0.05, scene.l_raw.shape)),
         f32(scene.opacity_logit + rng.normal(0.0, 0.1, scene.opacity_logit.shape)),
         f32(scene.sh + rng.normal(0.0, 0.05, scene.sh.shape)),
-        scene.sh_degree)
+        scene.sh_degree,
+        None if scene.lambda_raw is None else scene.lambda_raw.copy())
+
+
+# pre-sigmoid value of lambda_opa = 0.35, the initial value of section 5.1
+LAMBDA_RAW_INIT = -0.6190392084062235
+
+
+def with_learnable_lambda(scene: Scene, seed: int, spread: float = 0.5) -> Scene:
+    """Copy of ``scene`` with a per-Gaussian lambda_opa plane drawn around 0.35."""
+    rng = np.random.default_rng(seed)
+    out = dataclasses.replace(scene)
+    out.lambda_raw = np.ascontiguousarray(LAMBDA_RAW_INIT + rng.normal(0.0, spread, scene.n), dtype=np.float32)
+    return out
 
 
 RES_CHOICES = [(256, 256), (512, 384), (800, 800), (1024, 768)]
@@ -277,6 +295,47 @@ def make_workload(config: int, n_override: int | None = None) -> Workload:
     else:
         raise ValueError(f"unknown workload {config}")
     return Workload(CONFIG_NAMES[config], scene, cams, seed=seed)
+
+
+def scene_volume(n, seed, radius=0.6, sh_degree=3):
+    """Volumetric-medium stand-in: positions normally spread in a ball of
+    ~radius, position sigma ~0.8x the mean point spacing (so the medium is
+    covered), lower opacities (logit ~ N(-1, 1))."""
+    rng = np.random.default_rng(seed)
+    mu_p = rng.normal(0.0, radius / 1.7, (3, n))
+    r = np.linalg.norm(mu_p, axis=0, keepdims=True)
+    mu_p = np.where(r > 1.0, mu_p / r, mu_p)
+    spacing = (4.0 / 3.0 * math.pi * radius ** 3 / n) ** (1.0 / 3.0)
+    sc = _scene_common(rng, n, mu_p, pos_sigma=0.8 * spacing, pos_off_sigma=0.3 * spacing, sh_degree=sh_degree)
+    sc.opacity_logit = np.ascontiguousarray(rng.normal(-1.0, 1.0, n), dtype=np.float32)
+    return sc
+
+
+# Point counts and square image sides of the six scenes of the paper's
+# Table 2 (forward-only FPS; section 5.2), with the kind of content each
+# holds.  The scenes rendered here are synthetic stand-ins of those shapes;
+# the last field is the FPS the paper prints for 6DGS (hardware not named).
+TABLE2_SHAPES = [
+    ("vol6.7k_1408sq", 6660, 1408, "volume", 178.4),
+    ("vol12.7k_1408sq", 12657, 1408, "volume", 178.2),
+    ("vol17.1k_1024sq", 17133, 1024, "volume", 120.2),
+    ("vol10.8k_1536sq", 10762, 1536, "volume", 138.6),
+    ("surf175k_1408sq", 174746, 1408, "surface", 34.7),
+    ("vol183k_1024sq", 182981, 1024, "volume", 276.8),
+]
+TABLE2_SEED_BASE = 7000
+TABLE2_TEST_VIEWS = 20
+
+
+def table2_workload(index: int, n_override: int | None = None, views: int = TABLE2_TEST_VIEWS) -> Workload:
+    """Inference workload shaped like row ``index`` of Table 2: the scene and
+    ``views`` test cameras of that image size on a hemisphere of radius 4."""
+    name, n, side, kind, _ = TABLE2_SHAPES[index]
+    seed = TABLE2_SEED_BASE + index
+    n = n_override or n
+    scene = scene_volume(n, seed) if kind == "volume" else scene_shell(n, seed)
+    cams = hemisphere_cameras(views, [(side, side)] * views)
+    return Workload(name, scene, cams, seed=seed)
 
 
 def target_seed(config: int) -> int:

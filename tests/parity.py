@@ -162,3 +162,14 @@ def compare_tile_image(gpu_block, prep, cam, st, x, y, certain, possible):
             err = np.where(np.isnan(e), err, np.minimum(err, e))
         best = err if best is None else np.minimum(best, err)
     return best
+
+
+def assert_within(err, bound, what=""):
+    """Every |error| strictly below its bound (bound broadcast to err's shape)."""
+    err = np.asarray(err, dtype=np.float64)
+    bound = np.broadcast_to(np.asarray(bound, dtype=np.float64), err.shape)
+    bad = ~(err < bound)
+    if bad.any():
+        i = np.unravel_index(np.argmax(np.where(bad, err / np.maximum(bound, 1e-300), -np.inf)), err.shape)
+        raise AssertionError(f"{what}: {int(bad.sum())} of {err.size} above bound; worst at {i}: "
+                             f"{err[i]:.3e} vs {bound[i]:.3e}")

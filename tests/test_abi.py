@@ -100,3 +100,51 @@ def test_stage_calls_reject_small_workspace_without_touching_the_gpu():
     assert lib.sixdgs_bin_sort(ctypes.byref(plan), fake, 16, None, None) == _lib.ERR_WORKSPACE
     assert lib.sixdgs_bin_sort(ctypes.byref(plan), ctypes.c_void_p(257), plan.ws_bytes, None, None) == \
         _lib.ERR_INVALID_ARG
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirrors have the size and field offsets of the C structs."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sixdgs_camera": _lib.Camera, "sixdgs_scene": _lib.Scene, "sixdgs_settings": _lib.Settings,
+               "sixdgs_plan": _lib.Plan}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sixdgs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, value = line.split()
+        py = structs[cname]
+        got = ctypes.sizeof(py) if field == "sizeof" else getattr(py, field).offset
+        assert got == int(value), (cname, field)
+
+
+def test_inference_plan_has_no_gradient_section():
+    cams = synth.ring_cameras(2, 128, 128)
+    code, train = _plan(cams, n=5000)
+    code_i, inf = _plan(cams, n=5000, inference=True)
+    assert code == _lib.OK and code_i == _lib.OK
+    assert inf.off[_lib.WS_RANGES] == inf.off[_lib.WS_GRADREC]           # zero-sized section
+    assert train.ws_bytes - inf.ws_bytes >= 48 * train.n_pairs - 256
+    assert _plan(cams, n=5000, inference=True, store_aux=True)[0] == _lib.ERR_INVALID_ARG
+    lib = _lib.load()
+    # every backward entry point refuses an inference plan on the host
+    fake = ctypes.c_void_p(256)
+    sc = _lib.Scene()
+    sc.n, sc.sh_degree = 5000, 3
+    assert lib.sixdgs_blend_bwd(ctypes.byref(inf), fake, inf.ws_bytes, fake, fake, None, None) == \
+        _lib.ERR_INVALID_ARG
+    assert lib.sixdgs_raster_bwd(ctypes.byref(inf), ctypes.byref(sc), fake, inf.ws_bytes, fake, fake, fake,
+                                 fake, fake, fake, fake, None, 0, None, None) == _lib.ERR_INVALID_ARG
+    assert lib.sixdgs_project_bwd(ctypes.byref(inf), ctypes.byref(sc), fake, inf.ws_bytes, fake, fake, fake,
+                                  fake, fake, None, 0, None, None) == _lib.ERR_INVALID_ARG

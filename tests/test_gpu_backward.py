@@ -109,3 +109,59 @@ def test_autograd_function_matches_direct_call():
     direct = r2.backward(params, img2, g_img)
     for k in GROUPS:
         torch.testing.assert_close(leaves[k].grad, direct[k], rtol=1e-4, atol=1e-9)
+
+
+def test_learnable_lambda_forward_and_gradients():
+    """Per-Gaussian lambda_opa = sigmoid(raw) (section 4.2): images and every
+    gradient, lambda_raw included."""
+    scene = synth.with_learnable_lambda(synth.scene_shell(3000, 71, dp_sigma=0.1), 5, spread=1.0)
+    scene.l_raw[:3] += math.log(3.0)
+    cams = [synth.look_at_camera((4.0, 0.0, 0.5), 64, 56), synth.look_at_camera((0.0, -4.0, 0.0), 48, 64)]
+    st = O.Settings()
+    g_imgs = synth.random_grad_images(cams, 9)
+    r = sx.Renderer(scene.n, scene.sh_degree, cams, lambda_opa=0.9)   # global value unused
+    params = sx.params_to_device(scene)
+    img = r.forward(params)
+    for cam, im in zip(cams, r.split(img)):
+        ref, _ = O.render_view(scene, cam, st)
+        err = np.abs(im.cpu().numpy().astype(np.float64) - ref.numpy())
+        assert np.mean(err <= 2e-4) >= 0.999 and err.max() < 0.02, float(err.max())
+    g = r.backward(params, img, r.pack(g_imgs))
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in g.items()}
+    assert "lambda_raw" in gpu
+    ref = O.gradients(scene, cams, g_imgs, st)
+    groups = GROUPS + ("lambda_raw",)
+    for k in groups:
+        rel = np.linalg.norm(gpu[k].astype(np.float64) - ref[k]) / np.linalg.norm(ref[k])
+        assert rel <= REL_L2, (k, rel)
+
+
+def test_one_call_driver_equals_the_stages():
+    """sixdgs_render_batched = condition_project, bin_sort, raster_fwd (L1),
+    raster_bwd; forward-only without targets (also on an inference plan)."""
+    w = synth.make_workload(0)
+    tgt = synth.perturb(w.scene, synth.target_seed(0))
+    params = sx.params_to_device(w.scene)
+    r = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras)
+    targets = r.forward(sx.params_to_device(tgt))
+    img_s, gi_s, loss_s = r.forward(params, targets)
+    grads_s = r.backward(params, img_s, gi_s)
+    loss_s = float(loss_s.item())
+    img = r.new_images()
+    gi = torch.empty_like(img)
+    grads = r.new_grads(params)
+    r.status.zero_()
+    r.step(params, img, targets, gi, grads)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    assert torch.equal(img, img_s) and torch.equal(gi, gi_s)
+    assert abs(float(r.loss.item()) - loss_s) <= 1e-12 * abs(loss_s)
+    for k in GROUPS:      # equal up to the order of the record atomics
+        rel = float((grads[k] - grads_s[k]).norm() / grads_s[k].norm())
+        assert rel < 1e-5, (k, rel)
+    ri = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, inference=True)
+    img_i = ri.new_images()
+    ri.step(params, img_i)
+    torch.cuda.synchronize()
+    assert int(ri.status.item()) == 0 and torch.equal(img_i, img_s)

@@ -43,20 +43,19 @@ dist.init_process_group("gloo")
 r = dist.get_rank()
 bench.barrier(2)
 m = bench.max_over_ranks(1.5 + r, 2)
-print("RESULT", r, m, flush=True)
+with open(os.environ["OUT"] + "." + str(r), "w") as f:   # one file per rank: no interleaved stdout
+    f.write(f"{r} {m}")
 dist.destroy_process_group()
 '''
-    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", ROOT=ROOT)
     import tempfile
-    with tempfile.NamedTemporaryFile("w", suffix=".py", delete=False) as f:
-        f.write(code)
-        path = f.name
-    try:
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "ranks.py")
+        with open(path, "w") as f:
+            f.write(code)
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES="", ROOT=ROOT, OUT=os.path.join(tmp, "result"))
         cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
                "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), path]
         out = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, env=env, timeout=300)
-    finally:
-        os.unlink(path)
-    assert out.returncode == 0, out.stderr[-2000:]
-    res = sorted(ln.split()[1:] for ln in out.stdout.splitlines() if ln.startswith("RESULT"))
+        assert out.returncode == 0, out.stderr[-2000:]
+        res = sorted(open(os.path.join(tmp, f"result.{r}")).read().split() for r in range(2))
     assert res == [["0", "2.5"], ["1", "2.5"]]

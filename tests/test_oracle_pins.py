@@ -434,3 +434,113 @@ def test_gradients_match_finite_differences():
             nonzero += abs(ad) > 1e-8
     assert discarded <= 0.02 * (checked + discarded)
     assert nonzero > 100
+
+
+# --------------------------------------------------------------------------
+# Section 4.2: per-Gaussian learnable lambda_opa = sigmoid(raw)
+# --------------------------------------------------------------------------
+
+def test_constant_lambda_plane_equals_global_lambda():
+    scene = synth.scene_cube(300, 5)
+    scene.l_raw[:3] += math.log(3.0)
+    cam = synth.look_at_camera((4.0, 0.2, 0.1), 48, 40)
+    plane = synth.Scene(scene.mu_p, scene.mu_d, scene.l_raw, scene.opacity_logit, scene.sh, scene.sh_degree,
+                        np.full(scene.n, math.log(0.35 / 0.65), np.float32))
+    a, _ = O.render_view(scene, cam, O.Settings(lambda_opa=0.35))
+    lam_f32 = 1.0 / (1.0 + math.exp(-float(plane.lambda_raw[0])))   # the float32-stored raw value
+    b_ref, _ = O.render_view(scene, cam, O.Settings(lambda_opa=lam_f32))
+    b, _ = O.render_view(plane, cam, O.Settings(lambda_opa=0.9))   # global value ignored
+    np.testing.assert_allclose(b.numpy(), b_ref.numpy(), atol=1e-14)
+    np.testing.assert_allclose(b.numpy(), a.numpy(), atol=1e-6)
+
+
+def test_lambda_gradient_matches_finite_differences():
+    scene = synth.with_learnable_lambda(_fd_scene(), 12, spread=1.0)
+    cams = [synth.look_at_camera((4.0, 0.5, 0.3), 32, 32)]
+    st = O.Settings()
+    g_imgs = synth.random_grad_images(cams, 78)
+    grads = O.gradients(scene, cams, g_imgs, st)
+    base = np.asarray(scene.lambda_raw, dtype=np.float64)
+    checked = 0
+    for i in range(scene.n):
+        h = 1e-6 * max(1.0, abs(base[i]))
+        vals, sigs = [], []
+        for sgn in (+1, -1):
+            lam = base.copy()
+            lam[i] += sgn * h
+            sc = synth.Scene(scene.mu_p, scene.mu_d, scene.l_raw, scene.opacity_logit, scene.sh, scene.sh_degree, lam)
+            v, sg = _loss_and_decisions(sc, cams, st, g_imgs)
+            vals.append(v)
+            sigs.append(sg)
+        if sigs[0] != sigs[1]:
+            continue
+        fd = (vals[0] - vals[1]) / (2 * h)
+        ad = grads["lambda_raw"][i]
+        assert abs(fd - ad) <= 1e-6 * abs(ad) + 1e-8, (i, fd, ad)
+        checked += 1
+    assert checked >= scene.n - 1 and np.abs(grads["lambda_raw"]).max() > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Section 4.3, Algorithm 1 steps 4-5: scale and rotation of Sigma_cond
+# --------------------------------------------------------------------------
+
+def _rodrigues(axis, angle):
+    k = np.asarray(axis, dtype=np.float64)
+    k = k / np.linalg.norm(k)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+def test_scale_rotation_recovers_known_ellipsoid():
+    rng = np.random.default_rng(5)
+    Qs, ss = [], []
+    for _ in range(16):
+        Qs.append(_rodrigues(rng.normal(size=3), rng.uniform(0.1, 3.0)))
+        ss.append(rng.permutation([0.5, 0.05, 0.005]) * rng.uniform(0.5, 2.0))
+    Q = np.stack(Qs)
+    s = np.stack(ss)
+    S = torch.as_tensor(Q @ (s[:, :, None] ** 2 * np.transpose(Q, (0, 2, 1))))
+    R, scale = O.scale_rotation(S)
+    R, scale = R.numpy(), scale.numpy()
+    order = np.argsort(-s, axis=1)
+    np.testing.assert_allclose(scale, np.take_along_axis(s, order, 1), rtol=1e-10)
+    for i in range(16):
+        Qo = Q[i][:, order[i]]
+        # each column is the ellipsoid axis of that scale, up to its sign
+        np.testing.assert_allclose(np.abs(np.sum(R[i] * Qo, axis=0)), 1.0, rtol=1e-10)
+        assert abs(np.linalg.det(R[i]) - 1.0) < 1e-12
+
+
+def test_scale_rotation_matches_svd_and_reconstructs():
+    scene = _coupled_scene(n=128, seed=21, dp=0.3)
+    _, S = _sigma(scene)
+    _, _, S_cond = O.condition(S)
+    R, scale = O.scale_rotation(S_cond)
+    U, sv, _ = np.linalg.svd(S_cond.numpy())
+    np.testing.assert_allclose(scale.numpy() ** 2, sv, rtol=1e-9)
+    np.testing.assert_allclose(np.abs(np.einsum("nij,nij->nj", R.numpy(), U)), 1.0, rtol=1e-6)
+    rebuilt = R @ torch.diag_embed(scale ** 2) @ R.transpose(1, 2)
+    np.testing.assert_allclose(rebuilt.numpy(), S_cond.numpy(), rtol=1e-9, atol=1e-16)
+    np.testing.assert_allclose(np.linalg.det(R.numpy()), 1.0, atol=1e-12)
+    np.testing.assert_allclose(R.transpose(1, 2) @ R, np.broadcast_to(np.eye(3), (128, 3, 3)), atol=1e-12)
+
+
+def test_scale_rotation_axis_aligned_case():
+    d = np.array([[4.0, 9.0, 1.0], [1e-4, 1e-6, 1e-2]])
+    R, scale = O.scale_rotation(torch.as_tensor(np.stack([np.diag(r) for r in d])))
+    np.testing.assert_allclose(scale.numpy(), np.sqrt(-np.sort(-d, axis=1)), rtol=1e-12)
+    np.testing.assert_allclose(np.abs(R.numpy()).sum(axis=1), 1.0, atol=1e-12)  # signed permutation
+    np.testing.assert_allclose(np.linalg.det(R.numpy()), 1.0, atol=1e-12)
+
+
+def test_symmetric_eigen_matches_lapack():
+    rng = np.random.default_rng(8)
+    M = rng.normal(size=(64, 3, 3))
+    S = M @ np.transpose(M, (0, 2, 1))
+    S[:8] = np.diag([2.0, 2.0, 0.5])            # repeated eigenvalue
+    w, V = O.symmetric_eigen(torch.as_tensor(S))
+    w, V = w.numpy(), V.numpy()
+    np.testing.assert_allclose(np.sort(w, axis=1), np.linalg.eigvalsh(S), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(np.einsum("nik,nk,njk->nij", V, w, V), S, atol=1e-12)
+    np.testing.assert_allclose(np.einsum("nki,nkj->nij", V, V), np.broadcast_to(np.eye(3), S.shape), atol=1e-13)
