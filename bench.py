@@ -221,6 +221,8 @@ def measure_scale_rotation(l_raw, flush, steps=20, big_n=1 << 22):
     """Time the per-Gaussian scale / rotation extraction on the scene's own
     Gaussians and on a 4M-Gaussian tiling of them (larger than L2).  Algorithmic
     bytes per Gaussian: 21 raw Cholesky floats read, 9 + 3 floats written."""
+    import paper_2410_04974_gb300 as sx
+
     peak = hbm_peak()
     out = {}
     reps = -(-big_n // l_raw.shape[1])
