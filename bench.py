@@ -55,7 +55,8 @@ L2_FLUSH_BYTES = 256 << 20
 FLOPS_EVAL = 10
 FLOPS_COMP_FWD = 10
 FLOPS_COMP_BWD = 60
-MUFU_PER_COMP_FWD = 1
+MUFU_EVAL_FWD = 1        # ex2 per evaluated (pixel, entry) pair (branch-free loop)
+MUFU_EVAL_BWD = 2        # ex2 and the reciprocal of 1 - alpha
 SMS = 152
 FP32_LANES_PER_SM = 128
 SCALE_ROT_BYTES = (21 + 9 + 3) * 4
@@ -66,7 +67,7 @@ SCALE_ROT_BYTES = (21 + 9 + 3) * 4
 KERNEL_SOURCES = {
     "blend_bwd_kernel": ["raster.cu"], "blend_fwd_kernel": ["raster.cu"],
     "project_fwd_kernel": ["project.cu", "cond.cuh", "sh.cuh", "mat3.cuh"],
-    "onesweep_kernel": ["sort.cu"], "emit_kernel": ["sort.cu"],
+    "onesweep_kernel": ["sort.cu"], "emit_expand_kernel": ["sort.cu"],
     "geom_bwd_kernel": ["project_bwd.cu", "cond.cuh", "mat3.cuh"],
 }
 
@@ -113,6 +114,12 @@ def parse():
                     help="use --tile/--batch as given instead of the autotuner's pick")
     ap.add_argument("--tune-tiles", action="store_true",
                     help="let the autotuner also choose the tile shape (changes the render's tile lists)")
+    ap.add_argument("--profile-inference", type=int, default=0,
+                    help="run this many single-camera inference frames of the 174,746-point "
+                         "Table-2-shaped scene (no timing; for ncu) and exit")
+    ap.add_argument("--profile-scale-rotation", action="store_true",
+                    help="run the scale / rotation extraction on the 4M-Gaussian tiling of the workload's "
+                         "scene three times (no timing; for ncu) and exit")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many batched steps eagerly and exit (for ncu)")
     return ap.parse_args()
@@ -355,6 +362,33 @@ def measure_inference(flush, reps=10, views=synth.TABLE2_TEST_VIEWS):
             "paper_hardware": "not named in the paper", "scenes": out}
 
 
+def measure_alu_peaks(reps=5):
+    """Achieved FP32 FMA (TFLOP/s) and MUFU ex2 (Tops/s) rates of the library's
+    saturating probe kernels, best of `reps`, at the GPU's current clocks."""
+    import ctypes
+
+    import paper_2410_04974_gb300 as sx
+
+    lib = sx._lib.load()
+    blocks = SMS * 8
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    res = {}
+    for kind, iters, name, ops_per in ((0, 4096, "fp32_fma_tflops", 2.0), (1, 512, "mufu_ex2_tops", 1.0)):
+        best = float("inf")
+        for _ in range(reps + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sx._lib.check(lib.sixdgs_peak_probe(kind, iters, ctypes.c_void_p(out.data_ptr()), blocks, stream),
+                          "sixdgs_peak_probe")
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        res[name] = round(blocks * 256 * iters * 8 * ops_per / (best * 1e-3) / 1e12, 2)
+    return res
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -365,9 +399,10 @@ def hbm_peak():
 
 def launches_per_frame(plan, n_cams):
     """Kernels of ours one fwd+bwd frame launches: camera upload (one per 48
-    cameras), projection, compaction, depth passes, emission, tile passes,
-    ranges, blend forward, blend backward, SH backward, geometry backward."""
-    return (n_cams + 47) // 48 + 1 + 1 + plan.depth_passes + 1 + plan.tile_passes + 1 + 1 + 1 + 1 + 1
+    cameras), projection, compaction, depth passes, emission (scan + expand),
+    tile passes, ranges, blend forward, blend backward, SH backward, geometry
+    backward."""
+    return (n_cams + 47) // 48 + 1 + 1 + plan.depth_passes + 2 + plan.tile_passes + 1 + 1 + 1 + 1 + 1
 
 def build_inputs(args):
     w = synth.make_workload(args.config, n_override=args.n or None)
@@ -590,10 +625,16 @@ def run_ours(args, world, rank, local):
     peak = SMS * FP32_LANES_PER_SM * 2 * peak_clock * 1e6 / 1e12
     achieved = flops / (dom_ms * 1e-3) / 1e12
     kernel = {"raster_fwd": "blend_fwd_kernel", "blend_bwd": "blend_bwd_kernel"}[dom]
+    measured = measure_alu_peaks()
+    mufu = n_eval * (MUFU_EVAL_FWD if dom == "raster_fwd" else MUFU_EVAL_BWD) / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kernel, w.name),
                 "peak_basis": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                               f"{peak_clock:.0f} MHz (median SM clock under load)",
+                "measured_peaks": measured,
+                "frac_of_measured_fp32": round(achieved / measured["fp32_fma_tflops"], 4),
+                "mufu_achieved_tops": round(mufu, 3),
+                "frac_of_measured_mufu": round(mufu / measured["mufu_ex2_tops"], 4),
                 "pairs_evaluated": n_eval, "pairs_compositing": n_comp, "warp_entries": n_warp,
                 "kernel_ms": round(dom_ms, 4)}
 
@@ -604,7 +645,7 @@ def run_ours(args, world, rank, local):
     # ---- CPU baseline: the oracle on a bounded sample (rank 0) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(w, samples=1)
+        cpu = oracle_baseline(w, samples=1, sample_tiles=128)
 
     value = V * 1000.0 / ms_batched * world
     line = {
@@ -620,6 +661,8 @@ def run_ours(args, world, rank, local):
                    "visible_pairs": int(counts[0]), "duplicates": int(counts[1]), "dup_capacity": int(cap),
                    "autotuned": None if tuned is None else {k: tuned[k] for k in ("tile", "batch", "persistent",
                                                                                  "ms", "cached")}},
+        "megapixels_per_s": round(r.total_pixels * world / (ms_batched * 1e-3) / 1e6, 1),
+        "ms_per_step_median": round(max_over_ranks(statistics.median(t_batched), world), 4),
         "plain": plain, "speedup_vs_plain": round(plain["ms_per_step"] / ms_batched, 3) if plain else None,
         "batched_vs_plain": equiv, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
         "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
@@ -643,7 +686,10 @@ def oracle_baseline(w, samples=1, sample_tiles=8, seed=0):
     One sample = for one camera of the workload: the full per-Gaussian slice,
     colour and projection of every Gaussian (no grad), plus forward and
     backward (autograd) of `sample_tiles` tiles; the per-tile cost is scaled
-    to the camera's tiles with a non-empty list."""
+    to the camera's tiles with a non-empty list.  The oracle's cost per tile
+    grows with the number of Gaussians its autograd graph holds, so a larger
+    sample measures it slower: the extrapolation is an upper bound on the
+    oracle's views/s."""
     from oracle import sixdgs_oracle as O
 
     st = O.Settings(tile_w=16, tile_h=16, lambda_opa=w.lambda_opa, bg=w.bg)
@@ -678,7 +724,8 @@ def oracle_baseline(w, samples=1, sample_tiles=8, seed=0):
     return {"value": round(1.0 / view_s, 6), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
             "sample": f"{samples} view(s) of {w.name}: per-Gaussian slice/projection of all {w.scene.n} "
                       f"Gaussians + fwd/bwd of {sample_tiles} occupied 16x16 tiles, scaled to the view's "
-                      f"occupied tiles ({float(np.mean([len(occ)])):.0f})",
+                      f"occupied tiles ({float(np.mean([len(occ)])):.0f}); linear extrapolation, an upper "
+                      f"bound on the oracle's views/s",
             "seconds_measured": round(total, 2)}
 
 
@@ -707,9 +754,39 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def profile_inference(frames):
+    """Inference frames of one Table-2-shaped scene, untimed, for ncu captures."""
+    import paper_2410_04974_gb300 as sx
+
+    w = synth.table2_workload(4)
+    params = sx.params_to_device(w.scene)
+    params["cond_cache"] = sx.condition_cache(params)
+    r = sx.Renderer(w.scene.n, w.scene.sh_degree, [w.cameras[0]], inference=True)
+    img = r.new_images()
+    for f in range(frames):
+        r.set_cameras([w.cameras[f % len(w.cameras)]])
+        img = r.forward(params)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_inference": frames, "workload": w.name, "counts": r.counts().tolist()}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
+    if args.profile_inference:
+        profile_inference(args.profile_inference)
+        return
+    if args.profile_scale_rotation:
+        import paper_2410_04974_gb300 as sx
+
+        w, _ = build_inputs(args)
+        raw = torch.as_tensor(w.scene.l_raw).cuda()
+        big = raw.repeat(1, -(-(1 << 22) // raw.shape[1]))[:, :1 << 22].contiguous()
+        for _ in range(3):
+            _, _, status = sx.scale_rotation(big)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_scale_rotation": int(big.shape[1]), "status": int(status.item())}))
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -307,6 +307,15 @@ sixdgs_status sixdgs_render_batched(const sixdgs_plan* plan, const sixdgs_scene*
                                     float* grad_l_raw, float* grad_opacity_logit, float* grad_sh,
                                     float* grad_lambda_raw, int32_t* status_dev, sixdgs_stream_t stream);
 
+/* Measurement helper, no counterpart in the paper: `blocks` CTAs of 256
+ * threads each run `iters` iterations of 8 independent dependency chains of
+ * FP32 fused multiply-adds (kind 0: 2 flops each) or of MUFU ex2 plus one add
+ * (kind 1), and write one float per thread to out_dev (blocks * 256 floats,
+ * caller-owned device memory).  Timing the call gives the FP32-pipe and MUFU
+ * rates at the GPU's current clocks.  Errors: INVALID_ARG, CUDA. */
+sixdgs_status sixdgs_peak_probe(int32_t kind, int64_t iters, float* out_dev, int32_t blocks,
+                                sixdgs_stream_t stream);
+
 /* View-independent part of the slice (section 3.2, Eq. sigma; Algorithm 1
  * steps 1-3) for every Gaussian, stored for the cond_cache field of
  * sixdgs_scene: A = Sigma_pd Sigma_d^-1 (planes 0-8, row-major), the upper

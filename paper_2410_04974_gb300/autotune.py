@@ -23,7 +23,7 @@ import time
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sixdgs", "autotune.json")
 
 
-def candidate_space(tiles=((16, 16),), batches=(256, 512, 1024), persistent=(False, True)):
+def candidate_space(tiles=((16, 16),), batches=(128, 256, 512, 1024), persistent=(False, True)):
     out = []
     for t in tiles:
         for b in batches:

@@ -22,7 +22,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libsixdgs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "project.cu", "sort.cu", "raster.cu", "project_bwd.cu", "static_ws.cu", "scale_rotation.cu"]
+SOURCES = ["api.cu", "project.cu", "sort.cu", "raster.cu", "project_bwd.cu", "static_ws.cu", "scale_rotation.cu", "peak_probe.cu"]
 
 
 def nvcc() -> str:

@@ -27,7 +27,8 @@ enum {
   WS_DUP_A_V = 24,
   WS_DUP_B_K = 25,
   WS_DUP_B_V = 26,
-  WS_COUNT = 27
+  WS_CHUNK_FIRST = 27, // first pair of every emission chunk
+  WS_COUNT = 28
 };
 
 constexpr int kMaxCams = 256;
@@ -207,6 +208,7 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   take(WS_DUP_A_V, dup_capacity * 4);
   take(WS_DUP_B_K, dup_capacity * 4);
   take(WS_DUP_B_V, dup_capacity * 4);
+  take(WS_CHUNK_FIRST, (dup_capacity / kEmitChunk + 2) * 4);
   const bool odd = plan->tile_passes & 1;
   plan->off[SIXDGS_WS_SORTED] = plan->off[odd ? WS_DUP_B_V : WS_DUP_A_V];
   plan->off[SIXDGS_WS_SORTEDKEY] = plan->off[odd ? WS_DUP_B_K : WS_DUP_A_K];
@@ -331,6 +333,9 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
     a.n_pairs = (uint32_t)p->n_pairs;
     a.keys_out = ws_ptr<uint32_t>(ws, p, WS_DUP_A_K);
     a.vals_out = ws_ptr<uint32_t>(ws, p, WS_DUP_A_V);
+    // the depth keys are not needed once the depth passes are done
+    a.dup_off = ws_ptr<uint32_t>(ws, p, depth_in_a ? WS_DEPTH_A_K : WS_DEPTH_B_K);
+    a.chunk_first = ws_ptr<uint32_t>(ws, p, WS_CHUNK_FIRST);
     a.capacity = (uint64_t)p->dup_capacity;
     a.k_out = counts + 1;
     a.scan_state = ws_ptr<unsigned long long>(ws, p, WS_SCAN_E);
@@ -340,8 +345,10 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
     a.spin_budget = budget;
     a.status = status_dev;
     const int64_t tiles = (p->n_pairs + kScanTile - 1) / kScanTile;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 8));
-    launch_emit(a, grid, stream);
+    const int scan_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 8));
+    const int64_t chunks = (p->dup_capacity + kEmitChunk - 1) / kEmitChunk;
+    const int expand_grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)sms * 6));
+    launch_emit(a, scan_grid, expand_grid, stream);
   }
   // 4. tile passes
   const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->dup_capacity + kSortTile - 1) / kSortTile, (int64_t)sms * 4));
@@ -522,6 +529,13 @@ sixdgs_status sixdgs_render_batched(const sixdgs_plan* p, const sixdgs_scene* sc
   if (e != SIXDGS_OK || !train) return e;
   return sixdgs_raster_bwd(p, scene, ws, ws_bytes, images_dev, grad_images_dev, grad_mu_p, grad_mu_d,
                            grad_l_raw, grad_opacity_logit, grad_sh, grad_lambda_raw, 0, status_dev, stream);
+}
+
+sixdgs_status sixdgs_peak_probe(int32_t kind, int64_t iters, float* out_dev, int32_t blocks,
+                                sixdgs_stream_t stream) {
+  if ((kind != 0 && kind != 1) || iters < 0 || blocks < 1 || !out_dev) return SIXDGS_ERR_INVALID_ARG;
+  launch_peak_probe(kind, iters, out_dev, blocks, reinterpret_cast<cudaStream_t>(stream));
+  return launch_status();
 }
 
 sixdgs_status sixdgs_condition_cache(int64_t n, const float* l_raw_dev, const float* opacity_logit_dev,

@@ -70,6 +70,8 @@ struct EmitArgs {
   uint32_t n_pairs;
   uint32_t* keys_out;         // global tile id
   uint32_t* vals_out;         // pair index
+  uint32_t* dup_off;          // first output of each depth-sorted pair (n_vis)
+  uint32_t* chunk_first;      // pair owning the first output of each chunk
   uint64_t capacity;
   uint32_t* k_out;            // number of duplicates (may exceed capacity)
   unsigned long long* scan_state;
@@ -160,9 +162,10 @@ struct ScaleRotationArgs {
 void launch_project_fwd(const ProjectArgs& a, cudaStream_t stream);
 void launch_scale_rotation(const ScaleRotationArgs& a, cudaStream_t stream);
 void launch_cond_cache(const CondCacheArgs& a, cudaStream_t stream);
+void launch_peak_probe(int kind, int64_t iters, float* out, int blocks, cudaStream_t stream);
 void launch_compact(const CompactArgs& a, int grid, cudaStream_t stream);
 void launch_onesweep(const OnesweepArgs& a, int grid, cudaStream_t stream);
-void launch_emit(const EmitArgs& a, int grid, cudaStream_t stream);
+void launch_emit(const EmitArgs& a, int scan_grid, int expand_grid, cudaStream_t stream);
 void launch_ranges(const RangesArgs& a, int grid, cudaStream_t stream);
 void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
@@ -176,5 +179,6 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kEmitChunk = 2048;   // duplicates written per expansion chunk
 
 }  // namespace sixdgs

@@ -44,13 +44,26 @@ __global__ void __launch_bounds__(128) sh_bwd_kernel(ProjectBwdArgs a) {
     }
   float dmp[3] = {0.f, 0.f, 0.f};
   const float4* grec = reinterpret_cast<const float4*>(a.grad_rec);
+  // The next camera's tile count and colour gradients are loaded one
+  // iteration ahead (in bounds for every camera; ignored where the pair is
+  // not visible), so their latency overlaps this camera's arithmetic.
+  uint32_t nt_next = a.ntiles[g];
+  float4 gb_next = grec[g * 3 + 1];
+  float gbz_next = grec[g * 3 + 2].x;
   for (int v = 0; v < a.n_cams; ++v) {
-    const int64_t pair = (int64_t)v * n + g;
-    if (a.ntiles[pair] == 0u) continue;
-    const float4 gb = grec[pair * 3 + 1];
-    const float gbz = grec[pair * 3 + 2].x;
+    const uint32_t nt = nt_next;
+    const float4 gb = gb_next;
+    const float gbz = gbz_next;
+    if (v + 1 < a.n_cams) {
+      const int64_t next = (int64_t)(v + 1) * n + g;
+      nt_next = a.ntiles[next];
+      gb_next = grec[next * 3 + 1];
+      gbz_next = grec[next * 3 + 2].x;
+    }
+    if (nt == 0u) continue;
     const float drgb[3] = {gb.z, gb.w, gbz};
     if (drgb[0] == 0.f && drgb[1] == 0.f && drgb[2] == 0.f) continue;
+    const int64_t pair = (int64_t)v * n + g;
     const PairRec& r = a.rec[pair];
     const float rgb[3] = {r.b.z, r.b.w, r.c.x};
     const CamRec& cam = s_cams[v];
@@ -98,7 +111,7 @@ __global__ void __launch_bounds__(128) sh_bwd_kernel(ProjectBwdArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(128, 3) geom_bwd_kernel(ProjectBwdArgs a) {
   extern __shared__ CamRec s_cams[];
   for (int i = threadIdx.x; i < a.n_cams; i += blockDim.x) s_cams[i] = a.cams[i];
   __syncthreads();
@@ -126,11 +139,19 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(ProjectBwdArgs a) {
   float gmp[3] = {0.f, 0.f, 0.f}, gmd[3] = {0.f, 0.f, 0.f}, galpha = 0.f, glam = 0.f;
   const float4* grec = reinterpret_cast<const float4*>(a.grad_rec);
 
+  // next camera's count and record gradients loaded one iteration ahead
+  uint32_t nt_next = a.ntiles[g];
+  float4 ga_next = grec[g * 3], gb_next = grec[g * 3 + 1];
   for (int v = 0; v < a.n_cams && ok; ++v) {
-    const int64_t pair = (int64_t)v * n + g;
-    if (a.ntiles[pair] == 0u) continue;
-    const float4 ga = grec[pair * 3];
-    const float4 gb = grec[pair * 3 + 1];
+    const uint32_t nt = nt_next;
+    const float4 ga = ga_next, gb = gb_next;
+    if (v + 1 < a.n_cams) {
+      const int64_t next = (int64_t)(v + 1) * n + g;
+      nt_next = a.ntiles[next];
+      ga_next = grec[next * 3];
+      gb_next = grec[next * 3 + 1];
+    }
+    if (nt == 0u) continue;
     const CamRec& cam = s_cams[v];
     // ---- forward recomputation (same arithmetic as project_fwd_kernel) ----
     float dv[3] = {mp[0] - cam.campos[0], mp[1] - cam.campos[1], mp[2] - cam.campos[2]};

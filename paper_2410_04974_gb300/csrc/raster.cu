@@ -338,7 +338,10 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
         const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
         if (cmask) {
           float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
-          if (__popc(cmask) == 1) {   // one pixel: its own 9 atomics, no reduction
+          // Few pixels: their own 9 atomics each (one warp instruction per
+          // value whatever the number of lanes) beat the warp reduction; the
+          // threshold 4 was the fastest of 1, 2, 4, 8 and 32.
+          if (__popc(cmask) <= 4) {
             if (contrib) {
 #pragma unroll
               for (int k = 0; k < 9; ++k) red_add(dst + k, g[k]);

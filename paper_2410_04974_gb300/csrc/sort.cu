@@ -187,8 +187,18 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(OnesweepArgs a) 
   const uint32_t num_tiles = (n + kSortTile - 1) / kSortTile;
   // exclusive digit offsets of the whole pass (thread tid owns digit tid)
   uint32_t htot;
-  const uint32_t hist_excl = block_excl_scan<kSortThreads>(a.hist[tid], htot, s_warp);
+  const uint32_t my_count = a.hist[tid];
+  const uint32_t hist_excl = block_excl_scan<kSortThreads>(my_count, htot, s_warp);
   const uint32_t lt_mask = (1u << lane) - 1u;
+  // Every key has the same digit: the stable pass is the identity, so the
+  // tiles are copied through without ranking or look-back.
+  if (__syncthreads_or(n > 0u && my_count == n)) {
+    for (uint32_t i = blockIdx.x * kSortThreads + tid; i < n; i += gridDim.x * kSortThreads) {
+      a.keys_out[i] = a.keys_in[i];
+      a.vals_out[i] = a.vals_in[i];
+    }
+    return;
+  }
   while (true) {
     __syncthreads();
     if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
@@ -285,32 +295,33 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(OnesweepArgs a) 
 // --------------------------------------------------------------------------
 // 3. Duplicate emission in depth order + tile-digit histograms
 //
-// Load-balanced: after the block's scan of the tile counts, consecutive
-// threads write consecutive duplicates; each finds the pair it belongs to by
-// binary search over the block's prefix sums in shared memory, so stores are
-// coalesced and no thread loops over a large rectangle alone.
+// Two kernels, so that the work is spread over the duplicates, not over the
+// visible pairs (a few large Gaussians can own most of the duplicates):
+//   emit_scan_kernel   -- exclusive scan of the depth-sorted pairs' tile
+//                         counts (decoupled look-back): every pair's first
+//                         output, the pair owning the first output of every
+//                         chunk of kEmitChunk outputs, and the total K;
+//   emit_expand_kernel -- one chunk per CTA at a time: the chunk's pairs
+//                         (at most kEmitChunk + 1, since every visible pair
+//                         has at least one tile) are staged in shared
+//                         memory, then consecutive threads write consecutive
+//                         duplicates, each finding its pair by binary search
+//                         over the staged offsets, so stores are coalesced.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) emit_kernel(EmitArgs a) {
+__global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(EmitArgs a) {
   __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
-  __shared__ uint32_t s_start[kScanTile + 1];   // block-local first output of each element
-  __shared__ uint32_t s_pair[kScanTile];
-  __shared__ uint32_t s_base[kScanTile];        // key of the element's top-left tile
-  __shared__ uint32_t s_shape[kScanTile];       // rect width | tiles_x << 16
-  __shared__ uint32_t s_hist[4 * 256];
   __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_excl;
-  for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
   const uint32_t n_vis = *a.n_vis;
   const uint32_t num_tiles = (n_vis + kScanTile - 1) / kScanTile;
-  const int lane = threadIdx.x & 31;
+  const unsigned long long cap = a.capacity;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= num_tiles) break;
-    const uint32_t first = threadIdx.x * kScanItems;
-    const uint32_t base = tile * kScanTile + first;
+    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
     uint32_t cnt[kScanItems];
     uint32_t sum = 0;
 #pragma unroll
@@ -319,65 +330,112 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(EmitArgs a) {
       const uint32_t p = valid ? a.pairs[base + k] : 0u;
       valid = valid && p < a.n_pairs;
       cnt[k] = valid ? a.ntiles[p] : 0u;
-      s_pair[first + k] = p;
-      if (cnt[k]) {
-        const CamRec& cam = a.cams[p / (uint32_t)a.n];
-        const ushort4 r = a.rect[p];
-        s_base[first + k] = (uint32_t)cam.tile_offset + (uint32_t)r.z * (uint32_t)cam.tiles_x + r.x;
-        s_shape[first + k] = (uint32_t)(r.y - r.x) | ((uint32_t)cam.tiles_x << 16);
-      }
       sum += cnt[k];
     }
     uint32_t total;
-    uint32_t run = block_excl_scan<kScanThreads>(sum, total, s_warp);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      s_start[first + k] = run;
-      run += cnt[k];
-    }
-    if (threadIdx.x == 0) s_start[kScanTile] = total;
+    const uint32_t run = block_excl_scan<kScanThreads>(sum, total, s_warp);
     if (threadIdx.x < 32) {
       unsigned long long e = scan_lookback(a.scan_state, tile, total, a.spin_budget, a.status);
       if (threadIdx.x == 0) s_excl = e;
     }
     __syncthreads();
-    const unsigned long long gbase = s_excl;
-    for (uint32_t o0 = 0; o0 < total; o0 += kScanThreads) {
-      const uint32_t o = o0 + threadIdx.x;
-      const bool valid = o < total;
-      uint32_t key = 0xffffffffu, p = 0;
-      if (valid) {
-        // last element e with s_start[e] <= o (empty elements share starts)
-        int lo = 0, hi = kScanTile - 1;
+    unsigned long long off = s_excl + run;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < n_vis) {
+        a.dup_off[base + k] = (uint32_t)min(off, 0xffffffffull);
+        // chunk boundaries b in [off, off + cnt) below the capacity
+        const unsigned long long end = min(off + cnt[k], cap);
+        for (unsigned long long b = (off + kEmitChunk - 1) / kEmitChunk * kEmitChunk; b < end; b += kEmitChunk)
+          a.chunk_first[b / kEmitChunk] = base + k;
+      }
+      off += cnt[k];
+    }
+    if (tile == num_tiles - 1 && threadIdx.x == 0) {
+      const unsigned long long k_total = s_excl + total;
+      *a.k_out = (uint32_t)min(k_total, 0xffffffffull);
+      if (k_total > cap) raise_status(a.status, SIXDGS_ERR_CAPACITY);
+    }
+  }
+}
+
+// row = local / w for the small integers of a tile rectangle: a float
+// estimate corrected to the exact quotient.
+// (64-bit, so that the correction terminates for any 32-bit input; w >= 1).
+__device__ __forceinline__ uint32_t rect_row(uint32_t local, uint32_t w) {
+  uint64_t row = (uint64_t)__fdividef((float)local, (float)w);
+  while (row > 0u && row * w > local) --row;
+  while ((row + 1u) * w <= local) ++row;
+  return (uint32_t)row;
+}
+
+__global__ void __launch_bounds__(kScanThreads) emit_expand_kernel(EmitArgs a) {
+  constexpr int kMaxPairs = kEmitChunk + 1;
+  __shared__ uint32_t s_start[kMaxPairs];      // first output of each staged pair
+  __shared__ uint32_t s_pair[kMaxPairs];
+  __shared__ uint32_t s_base[kMaxPairs];       // key of the pair's top-left tile
+  __shared__ uint32_t s_shape[kMaxPairs];      // rect width | tiles_x << 16
+  __shared__ uint32_t s_hist[4 * 256];
+  for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_vis = *a.n_vis;
+  const uint32_t k_all = (uint32_t)min((unsigned long long)*a.k_out, (unsigned long long)a.capacity);
+  const uint32_t n_chunks = n_vis ? (k_all + kEmitChunk - 1) / kEmitChunk : 0u;
+  for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const uint32_t o0 = c * kEmitChunk;
+    const uint32_t o1 = min(k_all, o0 + kEmitChunk);
+    // Every visible pair owns at least one output, so a chunk spans at most
+    // kMaxPairs pairs.  The clamps keep every index in bounds even if the
+    // scan gave up on a look-back wait (then the status word already
+    // reports the timeout).
+    const uint32_t e0 = min(a.chunk_first[c], n_vis - 1);
+    uint32_t e1 = (c + 1 < n_chunks) ? a.chunk_first[c + 1] : n_vis - 1;
+    e1 = max(min(e1, n_vis - 1), e0);
+    const int m = (int)min(e1 - e0 + 1u, (uint32_t)kMaxPairs);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kScanThreads) {
+      const uint32_t e = e0 + i;
+      const uint32_t p = a.pairs[e];
+      s_start[i] = a.dup_off[e];
+      s_pair[i] = p;
+      uint32_t base = 0, shape = 1;
+      if (p < a.n_pairs) {
+        const CamRec& cam = a.cams[p / (uint32_t)a.n];
+        const ushort4 r = a.rect[p];
+        base = (uint32_t)cam.tile_offset + (uint32_t)r.z * (uint32_t)cam.tiles_x + r.x;
+        shape = max((uint32_t)(r.y - r.x), 1u) | ((uint32_t)cam.tiles_x << 16);
+      }
+      s_base[i] = base;
+      s_shape[i] = shape;
+    }
+    __syncthreads();
+    int lo_prev = 0;
+    for (uint32_t o1r = o0; o1r < o1; o1r += kScanThreads) {
+      const uint32_t o = o1r + threadIdx.x;
+      uint32_t key = 0xffffffffu;
+      if (o < o1) {
+        // last staged pair whose first output is <= o (outputs increase by
+        // kScanThreads per step, so the previous answer bounds this one)
+        int lo = lo_prev, hi = m - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (s_start[mid] <= o) lo = mid;
           else hi = mid - 1;
         }
+        lo_prev = lo;
         const uint32_t local = o - s_start[lo];
         const uint32_t shape = s_shape[lo];
         const uint32_t w = shape & 0xffffu, tiles_x = shape >> 16;
-        const uint32_t row = local / w;
+        const uint32_t row = rect_row(local, w);
         key = s_base[lo] + row * tiles_x + (local - row * w);
-        p = s_pair[lo];
-        const unsigned long long out = gbase + o;
-        if (out < a.capacity) {
-          a.keys_out[out] = key;
-          a.vals_out[out] = p;
-        } else {
-          key = 0xffffffffu;   // not stored: not counted
-        }
+        a.keys_out[o] = key;
+        a.vals_out[o] = s_pair[lo];
       }
       for (int q = 0; q < a.passes; ++q) {
         const uint32_t d = key == 0xffffffffu ? 256u : (key >> (8 * q)) & 255u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[q * 256 + d], __popc(peers));
       }
-    }
-    if (tile == num_tiles - 1 && threadIdx.x == 0) {
-      unsigned long long k_total = s_excl + total;
-      *a.k_out = (uint32_t)min(k_total, 0xffffffffull);
-      if (k_total > a.capacity) raise_status(a.status, SIXDGS_ERR_CAPACITY);
     }
   }
   __syncthreads();
@@ -404,8 +462,9 @@ void launch_compact(const CompactArgs& a, int grid, cudaStream_t stream) {
 void launch_onesweep(const OnesweepArgs& a, int grid, cudaStream_t stream) {
   onesweep_kernel<<<grid, kSortThreads, 0, stream>>>(a);
 }
-void launch_emit(const EmitArgs& a, int grid, cudaStream_t stream) {
-  emit_kernel<<<grid, kScanThreads, 0, stream>>>(a);
+void launch_emit(const EmitArgs& a, int scan_grid, int expand_grid, cudaStream_t stream) {
+  emit_scan_kernel<<<scan_grid, kScanThreads, 0, stream>>>(a);
+  emit_expand_kernel<<<expand_grid, kScanThreads, 0, stream>>>(a);
 }
 void launch_ranges(const RangesArgs& a, int grid, cudaStream_t stream) {
   ranges_kernel<<<grid, 256, 0, stream>>>(a);
