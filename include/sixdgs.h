@@ -247,6 +247,22 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* plan, void* ws_dev, size_t ws
                                 float* grad_images_dev, double* loss_dev,
                                 int32_t* status_dev, sixdgs_stream_t stream);
 
+/* Stages 3 + 4a fused for the L1 loss (section 4.4 keeps the 3DGS losses;
+ * L1 is the term used here): raster_fwd with targets, then blend_bwd of that
+ * loss, in one kernel.  Each pixel's dL/dC = sign(C - target) / M (M as in
+ * raster_fwd) is known when its forward walk ends, so its backward replay
+ * follows in the same CTA with C, dL/dC and the walk length in registers.
+ * Results equal raster_fwd (with targets) followed by sixdgs_blend_bwd, up to
+ * the order of the atomic additions into the record gradients.
+ * images_dev: written; targets_dev: required; grad_images_dev: optional
+ * (NULL: dL/dC is not stored); loss_dev: required, accumulated as in
+ * raster_fwd.  Follow with sixdgs_project_bwd for the parameter gradients.
+ * Errors: INVALID_ARG (also for an inference plan), WORKSPACE, CUDA. */
+sixdgs_status sixdgs_raster_fwd_bwd(const sixdgs_plan* plan, void* ws_dev, size_t ws_bytes,
+                                    float* images_dev, const float* targets_dev,
+                                    float* grad_images_dev, double* loss_dev,
+                                    int32_t* status_dev, sixdgs_stream_t stream);
+
 /* Stage 4 -- gradients of sum <grad_images, images> with respect to every
  * raw scene parameter, through the blend (replayed in sorted order, front
  * to back, with the suffix colour taken from the forward image), the
@@ -295,9 +311,10 @@ sixdgs_status sixdgs_project_bwd(const sixdgs_plan* plan, const sixdgs_scene* sc
  *   loss_dev and every grad_* are ignored and may be NULL; the plan may be an
  *   inference plan).
  * targets_dev != NULL: forward with the fused L1 loss, then the backward of
- *   that loss: *loss_dev (a double) is overwritten with the loss,
- *   grad_images_dev receives dL/dC, grad_* are overwritten as in
- *   sixdgs_raster_bwd (grad_lambda_raw as there).
+ *   that loss (sixdgs_raster_fwd_bwd, then sixdgs_project_bwd): *loss_dev (a
+ *   double) is overwritten with the loss, grad_images_dev (optional) receives
+ *   dL/dC, grad_* are overwritten as in sixdgs_raster_bwd (grad_lambda_raw as
+ *   there).
  * Errors: those of the stages; a capacity overflow is reported through
  * *status_dev by bin_sort as usual. */
 sixdgs_status sixdgs_render_batched(const sixdgs_plan* plan, const sixdgs_scene* scene,

@@ -58,6 +58,7 @@ EXPORTS = {
                                     c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sixdgs_blend_bwd": (c_int32, [ctypes.POINTER(Plan), c_void_p, c_size_t, c_void_p, c_void_p,
                                    c_void_p, c_void_p]),
+    "sixdgs_raster_fwd_bwd": (c_int32, [ctypes.POINTER(Plan), c_void_p, c_size_t] + [c_void_p] * 6),
     "sixdgs_render_batched": (c_int32, [ctypes.POINTER(Plan), ctypes.POINTER(Scene), ctypes.POINTER(Camera),
                                         c_void_p, c_size_t] + [c_void_p] * 12),
     "sixdgs_peak_probe": (c_int32, [c_int32, c_int64, c_void_p, c_int32, c_void_p]),

@@ -430,6 +430,23 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* p, void* ws, size_t ws_bytes,
   return launch_status();
 }
 
+sixdgs_status sixdgs_raster_fwd_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, float* images_dev,
+                                    const float* targets_dev, float* grad_images_dev, double* loss_dev,
+                                    int32_t* status_dev, sixdgs_stream_t stream_) {
+  sixdgs_status e = check_ws(p, ws, ws_bytes);
+  if (e != SIXDGS_OK) return e;
+  if (p->settings.inference || !images_dev || !targets_dev || !loss_dev) return SIXDGS_ERR_INVALID_ARG;
+  BlendArgs a = blend_args(p, ws);
+  a.images = images_dev;
+  a.targets = targets_dev;
+  a.grad_images = grad_images_dev;
+  a.loss = loss_dev;
+  a.grad_rec = ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
+  a.status = status_dev;
+  launch_blend_fused(a, p->total_tiles, reinterpret_cast<cudaStream_t>(stream_));
+  return launch_status();
+}
+
 sixdgs_status sixdgs_blend_bwd(const sixdgs_plan* p, void* ws, size_t ws_bytes, const float* images_dev,
                                const float* grad_images_dev, int32_t* status_dev, sixdgs_stream_t stream_) {
   sixdgs_status e = check_ws(p, ws, ws_bytes);
@@ -513,8 +530,7 @@ sixdgs_status sixdgs_render_batched(const sixdgs_plan* p, const sixdgs_scene* sc
   if (e != SIXDGS_OK) return e;
   const bool train = targets_dev != nullptr;
   if (train) {
-    if (p->settings.inference || !grad_images_dev || !loss_dev || !valid_scene(p, scene))
-      return SIXDGS_ERR_INVALID_ARG;
+    if (p->settings.inference || !loss_dev || !valid_scene(p, scene)) return SIXDGS_ERR_INVALID_ARG;
     if (p->n > 0 && (!grad_mu_p || !grad_mu_d || !grad_l_raw || !grad_opacity_logit || !grad_sh))
       return SIXDGS_ERR_INVALID_ARG;
     if (cudaMemsetAsync(loss_dev, 0, sizeof(double), reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
@@ -524,11 +540,12 @@ sixdgs_status sixdgs_render_batched(const sixdgs_plan* p, const sixdgs_scene* sc
   if (e != SIXDGS_OK) return e;
   e = sixdgs_bin_sort(p, ws, ws_bytes, status_dev, stream);
   if (e != SIXDGS_OK) return e;
-  e = sixdgs_raster_fwd(p, ws, ws_bytes, images_dev, targets_dev, train ? grad_images_dev : nullptr,
-                        train ? loss_dev : nullptr, status_dev, stream);
-  if (e != SIXDGS_OK || !train) return e;
-  return sixdgs_raster_bwd(p, scene, ws, ws_bytes, images_dev, grad_images_dev, grad_mu_p, grad_mu_d,
-                           grad_l_raw, grad_opacity_logit, grad_sh, grad_lambda_raw, 0, status_dev, stream);
+  if (!train) return sixdgs_raster_fwd(p, ws, ws_bytes, images_dev, nullptr, nullptr, nullptr, status_dev, stream);
+  e = sixdgs_raster_fwd_bwd(p, ws, ws_bytes, images_dev, targets_dev, grad_images_dev, loss_dev, status_dev,
+                            stream);
+  if (e != SIXDGS_OK) return e;
+  return sixdgs_project_bwd(p, scene, ws, ws_bytes, grad_mu_p, grad_mu_d, grad_l_raw, grad_opacity_logit,
+                            grad_sh, grad_lambda_raw, 0, status_dev, stream);
 }
 
 sixdgs_status sixdgs_peak_probe(int32_t kind, int64_t iters, float* out_dev, int32_t blocks,

@@ -168,6 +168,7 @@ void launch_onesweep(const OnesweepArgs& a, int grid, cudaStream_t stream);
 void launch_emit(const EmitArgs& a, int scan_grid, int expand_grid, cudaStream_t stream);
 void launch_ranges(const RangesArgs& a, int grid, cudaStream_t stream);
 void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
+void launch_blend_fused(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream);
 void launch_sh_bwd(const ProjectBwdArgs& a, cudaStream_t stream);
 void launch_geom_bwd(const ProjectBwdArgs& a, cudaStream_t stream);

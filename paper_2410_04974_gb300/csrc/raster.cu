@@ -109,31 +109,30 @@ __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, i
   }
 }
 
-// Forward blend of global tile gt by the calling CTA.
-template <bool kCount, bool kStore>
-__device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
+// Per-pixel front-to-back walk of a tile's list (the forward blend): T and
+// C accumulate over the entries that reach the warp's sub-block; walked is
+// the number of list entries before the stop (the list length if none).
+struct FwdPixel {
+  float T, C0, C1, C2;
+  uint32_t walked;
+  bool staged;   // the whole list was loaded as one batch (CTA-uniform)
+};
+
+template <bool kCount>
+__device__ __forceinline__ FwdPixel fwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
+                                             uint2 range, bool inside, float4* s_a, float4* s_b, float4* s_c,
+                                             uint32_t& n_eval, uint32_t& n_comp, uint32_t& n_warp) {
   const int B = a.batch;
-  float4* s_a = s_mem;
-  float4* s_b = s_mem + B;
-  float4* s_c = s_mem + 2 * B;
-  __shared__ float s_red[16];
-
-  const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
-  const uint32_t local = gt - (uint32_t)cam.tile_offset;
-  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
-  const bool inside = pm.px < cam.width && pm.py < cam.height;
-  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
-  const uint2 range = a.ranges[gt];
   const int lane = threadIdx.x & 31;
-
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   bool done = !inside;
   uint32_t walked = range.y - range.x;
-  uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
+  bool staged = false;
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
     load_batch(a, start, cnt, s_a, s_b, s_c);
+    staged = start == range.x && start + cnt == range.y;
     __syncthreads();
     if (__all_sync(0xffffffffu, done)) continue;
     for (int base = 0; base < cnt; base += 32) {
@@ -159,7 +158,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, 
         C1 = __fmaf_rn(rb.w, w, C1);
         C2 = __fmaf_rn(blue, w, C2);
         T = stop ? T : test_T;
-        if (kStore && stop) walked = start - range.x + j;
+        if (stop) walked = start - range.x + j;
         if (kCount) {
           n_eval += done ? 0u : 1u;
           n_comp += (vis && !stop) ? 1u : 0u;
@@ -169,6 +168,30 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, 
       if (__all_sync(0xffffffffu, done)) break;
     }
   }
+  return FwdPixel{T, C0, C1, C2, walked, staged};
+}
+
+// Forward blend of global tile gt by the calling CTA.
+template <bool kCount, bool kStore>
+__device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
+  const int B = a.batch;
+  float4* s_a = s_mem;
+  float4* s_b = s_mem + B;
+  float4* s_c = s_mem + 2 * B;
+  __shared__ float s_red[16];
+
+  const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
+  const uint32_t local = gt - (uint32_t)cam.tile_offset;
+  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
+  const bool inside = pm.px < cam.width && pm.py < cam.height;
+  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
+  const uint2 range = a.ranges[gt];
+  const int lane = threadIdx.x & 31;
+
+  uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
+  const FwdPixel fp = fwd_walk<kCount>(a, pm, pxc, pyc, range, inside, s_a, s_b, s_c, n_eval, n_comp, n_warp);
+  float T = fp.T, C0 = fp.C0, C1 = fp.C1, C2 = fp.C2;
+  const uint32_t walked = fp.walked;
 
   float l1 = 0.f;
   if (inside) {
@@ -249,38 +272,17 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
 }
 
-// Backward blend of global tile gt by the calling CTA.  kRecompute: re-derive
-// the stop from the transmittance (no per-pixel state); otherwise walk each
-// pixel's stored number of entries.
+// Backward replay of a tile's list for the calling thread's pixel, front to
+// back (as the forward), accumulating the record gradients of every entry.
+// kRecompute: re-derive the stop from the transmittance; otherwise the pixel
+// walks `bound` entries.  staged (CTA-uniform): the whole list is already in
+// shared memory (a single batch that the forward of the same CTA staged).
 template <bool kRecompute>
-__device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
+__device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
+                                         uint2 range, bool inside, const float* Cf, const float* dC,
+                                         uint32_t bound, bool staged, float4* s_a, float4* s_b, float4* s_c) {
   const int B = a.batch;
-  float4* s_a = s_mem;
-  float4* s_b = s_mem + B;
-  float4* s_c = s_mem + 2 * B;
-
-  const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
-  const uint32_t local = gt - (uint32_t)cam.tile_offset;
-  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
-  const bool inside = pm.px < cam.width && pm.py < cam.height;
-  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
-  const uint2 range = a.ranges[gt];
   const int lane = threadIdx.x & 31;
-
-  float Cf[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f};
-  uint32_t bound = range.y - range.x;
-  if (inside) {
-    const int64_t hw = (int64_t)cam.width * cam.height;
-    const int64_t pix = (int64_t)pm.py * cam.width + pm.px;
-    const float* img = a.images_in + 3 * cam.pixel_base;
-    const float* gi = a.grad_in + 3 * cam.pixel_base;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      Cf[ch] = img[ch * hw + pix];
-      dC[ch] = gi[ch * hw + pix];
-    }
-    if (!kRecompute) bound = a.nwalk[cam.pixel_base + pix];
-  }
   // dL/dalpha_i = sum_c dC_c (c_i T_i - S_c / (1 - alpha_i)) with S the colour
   // behind entry i, S_c = C_c - P_c (P the running front-to-back sum), so
   // sum_c dC_c S_c = D0 - Q with D0 = dC . C and Q = dC . P kept as a scalar.
@@ -291,7 +293,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
-    load_batch(a, start, cnt, s_a, s_b, s_c);
+    if (!staged) load_batch(a, start, cnt, s_a, s_b, s_c);
     __syncthreads();
     if (__all_sync(0xffffffffu, done)) continue;
     for (int base = 0; base < cnt; base += 32) {
@@ -356,6 +358,118 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
       }
       if (__all_sync(0xffffffffu, done)) break;
     }
+  }
+}
+
+// Backward blend of global tile gt by the calling CTA.  kRecompute: re-derive
+// the stop from the transmittance (no per-pixel state); otherwise walk each
+// pixel's stored number of entries.
+template <bool kRecompute>
+__device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
+  const int B = a.batch;
+
+  const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
+  const uint32_t local = gt - (uint32_t)cam.tile_offset;
+  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
+  const bool inside = pm.px < cam.width && pm.py < cam.height;
+  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
+  const uint2 range = a.ranges[gt];
+
+  float Cf[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f};
+  uint32_t bound = range.y - range.x;
+  if (inside) {
+    const int64_t hw = (int64_t)cam.width * cam.height;
+    const int64_t pix = (int64_t)pm.py * cam.width + pm.px;
+    const float* img = a.images_in + 3 * cam.pixel_base;
+    const float* gi = a.grad_in + 3 * cam.pixel_base;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      Cf[ch] = img[ch * hw + pix];
+      dC[ch] = gi[ch * hw + pix];
+    }
+    if (!kRecompute) bound = a.nwalk[cam.pixel_base + pix];
+  }
+  bwd_walk<kRecompute>(a, pm, pxc, pyc, range, inside, Cf, dC, bound, false, s_mem, s_mem + B, s_mem + 2 * B);
+}
+
+// Forward blend, fused L1 loss and backward blend of global tile gt by the
+// calling CTA, for the training step whose loss is the L1 term (section
+// 4.4): each pixel's dL/dC = sign(C - target) / M is known as soon as its
+// forward walk ends, so the backward replay follows in the same CTA with C,
+// dL/dC and the walk length in registers, and a list that fitted in one
+// batch is replayed from the shared memory the forward filled.  Images,
+// dL/dC, loss and record gradients equal those of raster_fwd followed by
+// blend_bwd in stored-walk mode, bit for bit up to the order of the atomic
+// additions.
+__device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
+  const int B = a.batch;
+  float4* s_a = s_mem;
+  float4* s_b = s_mem + B;
+  float4* s_c = s_mem + 2 * B;
+  __shared__ float s_red[16];
+
+  const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
+  const uint32_t local = gt - (uint32_t)cam.tile_offset;
+  const PixelMap pm = map_pixel(a.tile_w, local % cam.tiles_x, local / cam.tiles_x, a.tile_h);
+  const bool inside = pm.px < cam.width && pm.py < cam.height;
+  const float pxc = (float)pm.px + 0.5f, pyc = (float)pm.py + 0.5f;
+  const uint2 range = a.ranges[gt];
+  const int lane = threadIdx.x & 31;
+
+  uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
+  const FwdPixel fp = fwd_walk<false>(a, pm, pxc, pyc, range, inside, s_a, s_b, s_c, n_eval, n_comp, n_warp);
+  float Cf[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f};
+  float l1 = 0.f;
+  if (inside) {
+    Cf[0] = __fmaf_rn(fp.T, a.bg[0], fp.C0);
+    Cf[1] = __fmaf_rn(fp.T, a.bg[1], fp.C1);
+    Cf[2] = __fmaf_rn(fp.T, a.bg[2], fp.C2);
+    const int64_t hw = (int64_t)cam.width * cam.height;
+    const int64_t pix = (int64_t)pm.py * cam.width + pm.px;
+    float* img = a.images + 3 * cam.pixel_base;
+    const float* tg = a.targets + 3 * cam.pixel_base + pix;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      img[ch * hw + pix] = Cf[ch];
+      const float d = Cf[ch] - tg[ch * hw];
+      dC[ch] = d > 0.f ? a.inv_count : (d < 0.f ? -a.inv_count : 0.f);
+      l1 += fabsf(d);
+    }
+    if (a.grad_images) {
+      float* gi = a.grad_images + 3 * cam.pixel_base + pix;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) gi[ch * hw] = dC[ch];
+    }
+    if (a.nwalk) a.nwalk[cam.pixel_base + pix] = fp.walked;
+  }
+  l1 = warp_sum(l1);
+  if (lane == 0) s_red[threadIdx.x >> 5] = l1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += s_red[w];
+    atomicAdd(a.loss, sum * (double)a.inv_count);
+  }
+  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_a, s_b, s_c);
+}
+
+// 40 registers (6 CTAs of 256 threads per SM, as the separate kernels): with
+// only a 512-thread bound the compiler picks 40 and spills 44 bytes; capped
+// explicitly it spills 8 and ran 1-2% faster than both that and 48 or 70.
+__global__ void __maxnreg__(40) blend_fused_kernel(BlendArgs a) {
+  extern __shared__ float4 s_mem[];
+  if (!a.tile_queue) {
+    blend_fused_tile(a, blockIdx.x, s_mem);
+    return;
+  }
+  __shared__ uint32_t s_next;
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(a.tile_queue, 1u);
+    __syncthreads();
+    const uint32_t gt = s_next;
+    if (gt >= a.total_tiles) break;
+    blend_fused_tile(a, gt, s_mem);
+    __syncthreads();
   }
 }
 
@@ -439,6 +553,11 @@ void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stre
     if (a.nwalk) launch_blend(blend_fwd_kernel<false, true>, a, total_tiles, stream);
     else launch_blend(blend_fwd_kernel<false, false>, a, total_tiles, stream);
   }
+}
+
+void launch_blend_fused(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
+  if (total_tiles == 0) return;
+  launch_blend(blend_fused_kernel, a, total_tiles, stream);
 }
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {

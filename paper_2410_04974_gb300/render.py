@@ -163,6 +163,16 @@ class Renderer:
                                               _ptr(grad_images), _ptr(loss), _ptr(self.status),
                                               self._stream(stream)), "sixdgs_raster_fwd")
 
+    def raster_fwd_bwd(self, images, targets, grad_images=None, loss=None, stream=None):
+        """Forward blend, fused L1 loss and backward blend in one kernel
+        (sixdgs_raster_fwd_bwd); follow with project_bwd.  The loss
+        accumulates into `loss` (default: self.loss, not zeroed here)."""
+        ws, nb = self._wsargs()
+        loss = self.loss if loss is None else loss
+        _lib.check(self.lib.sixdgs_raster_fwd_bwd(ctypes.byref(self.plan), ws, nb, _ptr(images), _ptr(targets),
+                                                  _ptr(grad_images), _ptr(loss), _ptr(self.status),
+                                                  self._stream(stream)), "sixdgs_raster_fwd_bwd")
+
     def raster_bwd(self, params, images, grad_images, grads, accumulate=False, stream=None):
         ws, nb = self._wsargs()
         sc = self.scene_struct(params)

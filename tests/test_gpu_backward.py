@@ -165,3 +165,45 @@ def test_one_call_driver_equals_the_stages():
     ri.step(params, img_i)
     torch.cuda.synchronize()
     assert int(ri.status.item()) == 0 and torch.equal(img_i, img_s)
+
+
+@pytest.mark.parametrize("batch,persistent", [(512, False), (32, False), (64, True)])
+def test_fused_forward_backward_equals_separate_kernels(batch, persistent):
+    """sixdgs_raster_fwd_bwd (one kernel: forward, L1, backward replay from
+    registers and, for single-batch lists, from the staged shared memory)
+    against raster_fwd + blend_bwd: images, dL/dC and loss bit for bit, record
+    and parameter gradients up to the order of the atomic additions.  Batch 32
+    makes most lists span several batches (the reloading path)."""
+    w = synth.make_workload(0)
+    tgt = synth.perturb(w.scene, synth.target_seed(0))
+    params = sx.params_to_device(w.scene)
+    r = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, batch=batch, persistent=persistent)
+    targets = r.forward(sx.params_to_device(tgt))
+    img_s, gi_s, loss_s = r.forward(params, targets)
+    grads_s = r.backward(params, img_s, gi_s)
+    rec_s = r.grad_records().clone()
+    loss_s = float(loss_s.item())
+    ranges = r.ranges().cpu().numpy()
+    lengths = ranges[:, 1] - ranges[:, 0]
+    if batch == 32:
+        assert (lengths > 32).mean() > 0.3          # the multi-batch path is exercised
+    r.status.zero_()
+    r.loss.zero_()
+    r.condition_project(params)
+    r.bin_sort()
+    img = r.new_images()
+    gi = torch.empty_like(img)
+    r.raster_fwd_bwd(img, targets, gi)
+    grads = r.new_grads(params)
+    r.project_bwd(params, grads)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    assert torch.equal(img, img_s) and torch.equal(gi, gi_s)
+    assert abs(float(r.loss.item()) - loss_s) <= 1e-12 * abs(loss_s)
+    rec = r.grad_records()
+    vis = r.ntiles() > 0
+    scale = rec_s[vis].abs().amax(dim=0).clamp_min(1e-30)
+    assert float(((rec[vis] - rec_s[vis]).abs() / scale).max()) < 1e-5
+    for k in GROUPS:
+        rel = float((grads[k] - grads_s[k]).norm() / grads_s[k].norm())
+        assert rel < 1e-5, (k, rel)
