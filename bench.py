@@ -717,7 +717,8 @@ def run_ours(args, world, rank, local):
     # ---- CPU baseline: the oracle on a bounded sample (rank 0) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(w, samples=2, sample_tiles=None)
+        # two full views (one for views above a megapixel): about 10-40 s of oracle work
+        cpu = oracle_baseline(w, samples=1 if cams[0].width * cams[0].height > 1_000_000 else 2, sample_tiles=None)
 
     value = V * 1000.0 / ms_batched * world
     line = {

@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(128) cond_cache_kernel(CondCacheArgs a) {
 }
 
 template <bool kCached>
-__global__ void __launch_bounds__(128) project_fwd_kernel(ProjectArgs a) {
+// 4 CTAs per SM (128 registers, a few spilled) instead of 3: 0.115 -> 0.105 ms on
+// the 300k / 8 x 800^2 frame.
+__global__ void __launch_bounds__(128, 4) project_fwd_kernel(ProjectArgs a) {
   extern __shared__ CamRec s_cams[];
   for (int i = threadIdx.x; i < a.n_cams; i += blockDim.x) s_cams[i] = a.cams[i];
   __syncthreads();

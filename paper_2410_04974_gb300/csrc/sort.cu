@@ -172,7 +172,9 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(CompactArgs a) {
 // --------------------------------------------------------------------------
 // 2/4. One stable 8-bit digit pass (onesweep)
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(OnesweepArgs a) {
+// 80 registers, 3 CTAs per SM (2 at the unbounded 128): bin_sort 0.327 -> 0.320 ms
+// on the 300k / 8 x 800^2 frame.
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs a) {
   constexpr int WARPS = kSortThreads / 32;
   static_assert(kSortThreads == 256, "one thread per digit");
   __shared__ uint32_t s_whist[WARPS][256];

@@ -109,3 +109,22 @@ def test_nonfinite_cached_state_is_reported():
     torch.cuda.synchronize()
     assert int(r.status.item()) & (1 << sx._lib.ERR_NONFINITE)
     assert int(r.ntiles()[7]) == 0
+
+
+def test_cached_projection_with_learnable_lambda():
+    """The per-Gaussian lambda_opa plane is read beside the cached state: the
+    cached inference render equals the uncached one bit for bit."""
+    w = synth.table2_workload(1, n_override=8000, views=2)
+    scene = synth.with_learnable_lambda(w.scene, 77)
+    params = sx.params_to_device(scene)
+    assert "lambda_raw" in params
+    train = sx.Renderer(scene.n, scene.sh_degree, w.cameras)
+    img_t = train.forward(params)
+    inf = sx.Renderer(scene.n, scene.sh_degree, w.cameras, inference=True)
+    img_i = inf.forward(dict(params, cond_cache=sx.condition_cache(params)))
+    torch.cuda.synchronize()
+    assert int(inf.status.item()) == 0
+    assert torch.equal(img_t, img_i)
+    # and the plane matters: the global-lambda render differs
+    plain = {k: v for k, v in params.items() if k != "lambda_raw"}
+    assert not torch.equal(train.forward(plain), img_t)
