@@ -143,6 +143,16 @@ typedef struct sixdgs_settings {
                           the workspace, the projection writes no gradient
                           records, store_aux must be 0 and the backward entry
                           points return SIXDGS_ERR_INVALID_ARG                */
+  int32_t alpha_footprint; /* tile rectangle of a Gaussian: 0: the 3-sigma
+                          square of the 3DGS rasteriser that section 4.4 keeps;
+                          1: that square intersected with the bounding box of
+                          the Gaussian's alpha >= 1/255 ellipse (half-extents
+                          sqrt(2 ln(255 alpha_cond) Sigma2D_ii), widened by
+                          1e-4 relative + 0.01 px).  Tiles outside that box
+                          hold no pixel that composites the Gaussian, so images
+                          and gradients are the same with 1, and the tile lists
+                          shorter (about 40% fewer duplicates at 300k / 800^2) */
+  int32_t _pad;
 } sixdgs_settings;
 
 /* Sizes and workspace layout of one frame, filled by sixdgs_plan_init. */

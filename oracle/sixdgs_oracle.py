@@ -55,6 +55,10 @@ ALPHA_MAX = 0.99        # per-pixel alpha clamp
 T_MIN = 1e-4            # stop once transmittance would drop below this
 FRUSTUM_GUARD = 1.3     # x/z, y/z clamp (in units of the half-fov tangent) for J
 LAMBDA_OPA = 0.35       # section 5.1
+# tile footprint (settings.alpha_footprint = 1): the 3-sigma square intersected
+# with the bounding box of the alpha >= 1/255 ellipse, widened by these
+ALPHA_BOX_REL = 1e-4
+ALPHA_BOX_ABS = 0.01    # px
 
 
 @dataclasses.dataclass
@@ -63,6 +67,11 @@ class Settings:
     tile_h: int = 16
     lambda_opa: float = LAMBDA_OPA
     bg: tuple = (1.0, 1.0, 1.0)
+    # 1: tile rectangle = 3-sigma square (3DGS) intersected with the widened
+    # bounding box of the alpha >= 1/255 ellipse (tiles outside it hold no
+    # pixel that composites the Gaussian, so renders are unchanged); 0: the
+    # 3-sigma square alone
+    alpha_footprint: int = 1
 
 
 # ==========================================================================
@@ -271,18 +280,34 @@ def project(mu_cond, S_cond, cam):
     return t, torch.stack([u, v], dim=1), torch.stack([a, b, c], dim=1), det, conic, radius
 
 
-def tile_rect(mean2d, radius, cam, tile_w, tile_h):
-    """Tiles whose pixel span meets [u-r, u+r] x [v-r, v+r]: x in
-    [floor((u-r)/tw), floor((u+r)/tw)] clamped to the grid, same for y.
-    Returns int64 (n, 4): x0, x1 (exclusive), y0, y1 (exclusive)."""
+def tile_rect(mean2d, radius, cam, tile_w, tile_h, radius_y=None):
+    """Tiles whose pixel span meets [u-r, u+r] x [v-ry, v+ry] (ry = r unless
+    given): x in [floor((u-r)/tw), floor((u+r)/tw)] clamped to the grid, same
+    for y.  Returns int64 (n, 4): x0, x1 (exclusive), y0, y1 (exclusive)."""
+    ry = radius if radius_y is None else radius_y
     tiles_x = (cam.width + tile_w - 1) // tile_w
     tiles_y = (cam.height + tile_h - 1) // tile_h
     u, v = mean2d[:, 0], mean2d[:, 1]
     x0 = torch.floor((u - radius) / tile_w).clamp(0, tiles_x)
     x1 = (torch.floor((u + radius) / tile_w) + 1).clamp(0, tiles_x)
-    y0 = torch.floor((v - radius) / tile_h).clamp(0, tiles_y)
-    y1 = (torch.floor((v + radius) / tile_h) + 1).clamp(0, tiles_y)
+    y0 = torch.floor((v - ry) / tile_h).clamp(0, tiles_y)
+    y1 = (torch.floor((v + ry) / tile_h) + 1).clamp(0, tiles_y)
     return torch.stack([x0, x1, y0, y1], dim=1).to(torch.int64)
+
+
+def alpha_box(cov2d, alpha_cond):
+    """Half-extents (hx, hy) of the bounding box of the alpha >= 1/255 ellipse
+    {Delta : alpha_cond exp(-1/2 Delta^T conic Delta) >= 1/255}, i.e.
+    Delta^T Sigma2D^-1 Delta <= L2 = 2 ln(255 alpha_cond): sqrt(L2 Sigma2D_ii)
+    per axis (the extent of an ellipse along an axis), widened by
+    ALPHA_BOX_REL relative and ALPHA_BOX_ABS pixels.  Also returns
+    d(hx)/d(L2), d(hy)/d(L2), the sensitivity of each extent to L2."""
+    L2 = torch.clamp(2.0 * torch.log(255.0 * alpha_cond), min=0.0)
+    sx, sy = cov2d[:, 0], cov2d[:, 2]
+    hx = torch.sqrt(L2 * sx) * (1.0 + ALPHA_BOX_REL) + ALPHA_BOX_ABS
+    hy = torch.sqrt(L2 * sy) * (1.0 + ALPHA_BOX_REL) + ALPHA_BOX_ABS
+    root = torch.sqrt(torch.clamp(L2, min=1e-300))
+    return hx, hy, 0.5 * torch.sqrt(sx) / root, 0.5 * torch.sqrt(sy) / root
 
 
 # ==========================================================================
@@ -302,7 +327,9 @@ class ViewPrep:
     # decision margins (float64, no grad): distance of each cull/rect decision
     near_margin: torch.Tensor
     alpha_cond_logmargin: torch.Tensor
-    rect_edges: torch.Tensor  # (n, 4) (u-r)/tw, (u+r)/tw, (v-r)/th, (v+r)/th
+    rect_edges: torch.Tensor  # (n, 4) (u-ex)/tw, (u+ex)/tw, (v-ey)/th, (v+ey)/th
+    # d(extent)/d(L2) per axis where the alpha box sets the extent, else 0
+    rect_box_gain: torch.Tensor = None
 
 
 def to_params(scene, requires_grad=False, idx=None):
@@ -332,7 +359,15 @@ def prepare_view(p, sh_degree, cam, settings: Settings) -> ViewPrep:
     mu_cond, D, alpha_cond = slice_at(mu_p, mu_d, A, S_d_inv, alpha, d, lam)
     rgb = sh_colour(p["sh"], d, sh_degree)
     t, mean2d, cov2d, det, conic, radius = project(mu_cond, S_cond, cam)
-    rect = tile_rect(mean2d.detach(), radius.detach(), cam, settings.tile_w, settings.tile_h)
+    if settings.alpha_footprint:
+        hx, hy, gx, gy = alpha_box(cov2d.detach(), alpha_cond.detach())
+        ex, ey = torch.minimum(radius.detach(), hx), torch.minimum(radius.detach(), hy)
+        gain = torch.stack([torch.where(hx <= radius.detach() + ALPHA_BOX_ABS, gx, 0.0 * gx),
+                            torch.where(hy <= radius.detach() + ALPHA_BOX_ABS, gy, 0.0 * gy)], dim=1)
+    else:
+        ex = ey = radius.detach()
+        gain = torch.zeros((radius.shape[0], 2), dtype=radius.dtype)
+    rect = tile_rect(mean2d.detach(), ex, cam, settings.tile_w, settings.tile_h, ey)
     depth = t[:, 2]
     with torch.no_grad():
         ok_near = depth > cam.znear
@@ -341,12 +376,12 @@ def prepare_view(p, sh_degree, cam, settings: Settings) -> ViewPrep:
         ok_rect = (rect[:, 0] < rect[:, 1]) & (rect[:, 2] < rect[:, 3])
         valid = ok_near & ok_det & ok_alpha & ok_rect
         u, v = mean2d[:, 0], mean2d[:, 1]
-        r = radius
-        edges = torch.stack([(u - r) / settings.tile_w, (u + r) / settings.tile_w,
-                             (v - r) / settings.tile_h, (v + r) / settings.tile_h], dim=1)
+        edges = torch.stack([(u - ex) / settings.tile_w, (u + ex) / settings.tile_w,
+                             (v - ey) / settings.tile_h, (v + ey) / settings.tile_h], dim=1)
         prep = ViewPrep(depth, mean2d, conic, radius, alpha_cond, rgb, rect, valid,
                         (depth - cam.znear).detach(),
-                        (torch.log(alpha_cond) - math.log(ALPHA_MIN)).detach(), edges.detach())
+                        (torch.log(alpha_cond) - math.log(ALPHA_MIN)).detach(), edges.detach(),
+                        torch.nan_to_num(gain.detach(), nan=0.0, posinf=0.0))
     return prep
 
 

@@ -32,7 +32,7 @@ class Settings(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("lambda_opa", c_float),
                 ("bg", c_float * 3), ("store_aux", c_int32), ("spin_budget", c_int64),
                 ("loss_norm", c_float), ("count_pairs", c_int32), ("persistent", c_int32),
-                ("inference", c_int32)]
+                ("inference", c_int32), ("alpha_footprint", c_int32), ("_pad", c_int32)]
 
 
 class Plan(ctypes.Structure):

@@ -143,6 +143,7 @@ sixdgs_status sixdgs_plan_init(int64_t n, int32_t sh_degree, const sixdgs_camera
   if (!(st->lambda_opa >= 0.f) || !(st->lambda_opa <= 1.f)) return SIXDGS_ERR_INVALID_ARG;
   if (st->inference != 0 && st->inference != 1) return SIXDGS_ERR_INVALID_ARG;
   if (st->inference && st->store_aux) return SIXDGS_ERR_INVALID_ARG;
+  if (st->alpha_footprint != 0 && st->alpha_footprint != 1) return SIXDGS_ERR_INVALID_ARG;
   const int64_t n_pairs = (int64_t)n_cams * n;
   if (n_pairs >= ((int64_t)1 << 31)) return SIXDGS_ERR_INVALID_ARG;
   std::memset(plan, 0, sizeof(*plan));
@@ -249,6 +250,7 @@ sixdgs_status sixdgs_condition_project(const sixdgs_plan* p, const sixdgs_scene*
   a.lambda_opa = p->settings.lambda_opa;
   a.inv_tile_w = 1.f / (float)p->settings.tile_w;
   a.inv_tile_h = 1.f / (float)p->settings.tile_h;
+  a.alpha_footprint = p->settings.alpha_footprint;
   a.mu_p = scene->mu_p;
   a.mu_d = scene->mu_d;
   a.l_raw = scene->l_raw;

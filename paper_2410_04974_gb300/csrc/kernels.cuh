@@ -12,6 +12,7 @@ struct ProjectArgs {
   int32_t sh_degree;
   float lambda_opa;
   float inv_tile_w, inv_tile_h;
+  int32_t alpha_footprint;   // 1: tile rect within the alpha >= 1/255 box
   const float* mu_p;
   const float* mu_d;
   const float* l_raw;

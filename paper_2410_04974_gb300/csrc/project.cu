@@ -151,8 +151,19 @@ __global__ void __launch_bounds__(128, 4) project_fwd_kernel(ProjectArgs a) {
           float radius = kRadiusSigmas * sqrtf(lam);
           float u = cam.fx * t[0] * iz + cam.cx;
           float w = cam.fy * t[1] * iz + cam.cy;
-          float x0 = floorf((u - radius) * a.inv_tile_w), x1 = floorf((u + radius) * a.inv_tile_w) + 1.f;
-          float y0 = floorf((w - radius) * a.inv_tile_h), y1 = floorf((w + radius) * a.inv_tile_h) + 1.f;
+          // Bounding box of the alpha >= 1/255 ellipse {Delta^T conic Delta <=
+          // 2 ln(255 alpha_cond)}: half-extents sqrt(L2 * Sigma_2D,ii), widened
+          // by a margin far above FP32 rounding, so that culling with it (the
+          // tile rectangle here, the blend's per-warp test) never drops an
+          // entry that a pixel composites.
+          const float lo = log2f(alpha_cond);
+          const float L2 = 2.f * kLn2 * fmaxf(lo - kQMin, 0.f);
+          const float hx = sqrtf(L2 * ca) * 1.0001f + 0.01f;
+          const float hy = sqrtf(L2 * cc) * 1.0001f + 0.01f;
+          const float ex = a.alpha_footprint ? fminf(radius, hx) : radius;
+          const float ey = a.alpha_footprint ? fminf(radius, hy) : radius;
+          float x0 = floorf((u - ex) * a.inv_tile_w), x1 = floorf((u + ex) * a.inv_tile_w) + 1.f;
+          float y0 = floorf((w - ey) * a.inv_tile_h), y1 = floorf((w + ey) * a.inv_tile_h) + 1.f;
           x0 = fminf(fmaxf(x0, 0.f), (float)cam.tiles_x);
           x1 = fminf(fmaxf(x1, 0.f), (float)cam.tiles_x);
           y0 = fminf(fmaxf(y0, 0.f), (float)cam.tiles_y);
@@ -178,14 +189,6 @@ __global__ void __launch_bounds__(128, 4) project_fwd_kernel(ProjectArgs a) {
           }
           if (finite && x0 < x1 && y0 < y1) {
             ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
-            // Bounding box of the alpha >= 1/255 ellipse {Delta^T conic Delta <=
-            // 2 ln(255 alpha_cond)}: half-extents sqrt(L2 * Sigma_2D,ii), widened
-            // by a margin far above FP32 rounding so that culling with it never
-            // drops an entry that a pixel would composite.
-            const float lo = log2f(alpha_cond);
-            const float L2 = 2.f * kLn2 * fmaxf(lo - kQMin, 0.f);
-            const float hx = sqrtf(L2 * ca) * 1.0001f + 0.01f;
-            const float hy = sqrtf(L2 * cc) * 1.0001f + 0.01f;
             PairRec rec;
             rec.a = make_float4(u, w, -0.5f * kLog2e * con_a, -kLog2e * con_b);
             rec.b = make_float4(-0.5f * kLog2e * con_c, lo, rgb[0], rgb[1]);

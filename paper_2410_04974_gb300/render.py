@@ -39,7 +39,7 @@ def camera_array(cams):
 
 def make_settings(tile=(16, 16), batch=512, lambda_opa=0.35, bg=(1.0, 1.0, 1.0), store_aux=False,
                   spin_budget=0, loss_norm=0.0, count_pairs=False, persistent=False,
-                  inference=False) -> _lib.Settings:
+                  inference=False, alpha_footprint=True) -> _lib.Settings:
     s = _lib.Settings()
     s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
     s.batch = int(batch)
@@ -52,6 +52,7 @@ def make_settings(tile=(16, 16), batch=512, lambda_opa=0.35, bg=(1.0, 1.0, 1.0),
     s.count_pairs = 1 if count_pairs else 0
     s.persistent = 1 if persistent else 0
     s.inference = 1 if inference else 0
+    s.alpha_footprint = 1 if alpha_footprint else 0
     return s
 
 
@@ -88,7 +89,8 @@ class Renderer:
 
     def __init__(self, n, sh_degree, cameras, tile=(16, 16), batch=512, lambda_opa=0.35,
                  bg=(1.0, 1.0, 1.0), store_aux=False, dup_capacity=0, spin_budget=0, loss_norm=0.0,
-                 count_pairs=False, persistent=False, inference=False, device="cuda"):
+                 count_pairs=False, persistent=False, inference=False, alpha_footprint=True,
+                 device="cuda"):
         if not torch.cuda.is_available():
             raise _lib.SixDGSError("sixdgs needs a CUDA device; there is no CPU path")
         self.lib = _lib.load()
@@ -96,7 +98,7 @@ class Renderer:
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cameras = list(cameras)
         self.settings = make_settings(tile, batch, lambda_opa, bg, store_aux, spin_budget, loss_norm,
-                                      count_pairs, persistent, inference)
+                                      count_pairs, persistent, inference, alpha_footprint)
         self.cams = camera_array(self.cameras)
         self._make_plan(dup_capacity)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)

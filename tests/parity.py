@@ -21,6 +21,7 @@ from oracle import sixdgs_oracle as O
 # Rounding margins (FP32 decision value vs FP64): a decision is borderline
 # when its FP64 decision value is within these of the threshold.
 RECT_TOL_PX = 2e-3          # tile-rect edge (u +- r) vs a tile boundary, pixels
+L2_TOL = 4e-4               # 2 ln(255 alpha_cond) (the alpha box's squared scale), absolute
 LOG_ALPHA_COND_TOL = 1e-4   # ln(alpha_cond) vs ln(1/255)
 NEAR_TOL = 1e-5             # t_z vs znear
 DEPTH_REL_TOL = 1e-5        # relative depth gap of two list neighbours
@@ -40,12 +41,16 @@ def membership_sets(prep: O.ViewPrep, cam, settings):
     'possible' rect (member for some valid outcome)."""
     tx, ty = O.tile_grid(cam, settings)
     e = prep.rect_edges.numpy()
+    # where the alpha box sets an extent, its FP32 error follows that of
+    # L2 = 2 ln(255 alpha_cond) through d(extent)/d(L2)
+    gain = prep.rect_box_gain.numpy() if prep.rect_box_gain is not None else np.zeros((e.shape[0], 2))
+    tol = RECT_TOL_PX + L2_TOL * gain
     lim = [tx, tx, ty, ty]
     lo_hi = []
     for k in range(4):
         v = e[:, k]
         f = np.floor(v)
-        near_int = np.minimum(v - f, f + 1 - v) * (settings.tile_w if k < 2 else settings.tile_h) < RECT_TOL_PX
+        near_int = np.minimum(v - f, f + 1 - v) * (settings.tile_w if k < 2 else settings.tile_h) < tol[:, k // 2]
         nearest = np.round(v)
         alt = np.where(near_int, np.where(v - f < 0.5, f - 1, f + 1), f)  # the other floor value
         base = f + (1 if k in (1, 3) else 0)

@@ -231,3 +231,24 @@ def test_store_aux_does_not_change_the_image():
     _, _, a = _render(w.scene, w.cameras, store_aux=False)
     r, _, b = _render(w.scene, w.cameras, store_aux=True)
     torch.testing.assert_close(a, b, rtol=0, atol=0)
+
+
+def test_plain_three_sigma_footprint_and_equal_images():
+    """alpha_footprint=0 (the 3-sigma square of the 3DGS rasteriser) against
+    the oracle's same rule, and the default alpha-aware footprint gives the
+    same image bit for bit with fewer duplicates."""
+    w = synth.make_workload(0)
+    st = O.Settings(alpha_footprint=0)
+    params = sx.params_to_device(w.scene)
+    r0 = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, alpha_footprint=False)
+    img0 = r0.forward(params)
+    r1 = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras)
+    img1 = r1.forward(params)
+    torch.cuda.synchronize()
+    assert int(r0.status.item()) == 0 and int(r1.status.item()) == 0
+    prep, member = _check_records(r0, w.scene, w.cameras, st, 0)
+    _check_tiles(r0, w.scene, w.cameras, st, 0, _all_tiles(w.cameras[0], st), prep, member,
+                 img0.cpu().numpy().reshape(3, 128, 128))
+    assert torch.equal(img0, img1)
+    k0, k1 = int(r0.counts()[1]), int(r1.counts()[1])
+    assert k1 < 0.85 * k0, (k0, k1)

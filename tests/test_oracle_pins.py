@@ -337,11 +337,50 @@ def test_tiled_render_equals_brute_force(seed, w, h, tw, th):
     scene.mu_p *= 0.5
     scene.opacity_logit[:] = 2.0
     cam = synth.look_at_camera((4.0, 0.3, 0.2), w, h)
-    st = O.Settings(tile_w=tw, tile_h=th, lambda_opa=0.35, bg=(1.0, 0.9, 0.8))
-    img, prep = O.render_view(scene, cam, st)
-    assert int(prep.valid.sum()) >= 2
-    ref = _brute_force_image(prep, cam, st)
-    np.testing.assert_allclose(img.numpy(), ref, atol=1e-12)
+    # the per-pixel reference uses the 3DGS 3-sigma membership; both tile
+    # footprints must reproduce it (the alpha-aware one drops only tiles where
+    # the Gaussian composites no pixel)
+    st0 = O.Settings(tile_w=tw, tile_h=th, lambda_opa=0.35, bg=(1.0, 0.9, 0.8), alpha_footprint=0)
+    _, prep0 = O.render_view(scene, cam, st0)
+    assert int(prep0.valid.sum()) >= 2
+    ref = _brute_force_image(prep0, cam, st0)
+    for fp in (0, 1):
+        st = O.Settings(tile_w=tw, tile_h=th, lambda_opa=0.35, bg=(1.0, 0.9, 0.8), alpha_footprint=fp)
+        img, _ = O.render_view(scene, cam, st)
+        np.testing.assert_allclose(img.numpy(), ref, atol=1e-12)
+
+
+def test_alpha_footprint_keeps_every_compositing_pixel():
+    """Every pixel centre where a Gaussian's alpha reaches 1/255 lies in a
+    tile of its alpha-aware footprint, which is never larger than the 3-sigma
+    square and is much smaller on average."""
+    w = synth.make_workload(0)
+    cam = w.cameras[0]
+    p0 = O.prepare_view(O.to_params(w.scene), w.scene.sh_degree, cam, O.Settings(alpha_footprint=0))
+    p1 = O.prepare_view(O.to_params(w.scene), w.scene.sh_degree, cam, O.Settings(alpha_footprint=1))
+    assert torch.equal(p0.valid, p1.valid)
+    r0, r1 = p0.rect.numpy(), p1.rect.numpy()
+    v = p0.valid.numpy()
+    assert np.all(r1[v, 0] >= r0[v, 0]) and np.all(r1[v, 1] <= r0[v, 1])
+    assert np.all(r1[v, 2] >= r0[v, 2]) and np.all(r1[v, 3] <= r0[v, 3])
+    area = lambda r: np.maximum(r[:, 1] - r[:, 0], 0) * np.maximum(r[:, 3] - r[:, 2], 0)
+    assert area(r1[v]).sum() < 0.85 * area(r0[v]).sum()
+    m = p0.mean2d.detach().numpy()
+    con = p0.conic.detach().numpy()
+    ac = p0.alpha_cond.detach().numpy()
+    checked = 0
+    for g in np.nonzero(v)[0]:
+        x0, x1, y0, y1 = r0[g]
+        px = np.arange(x0 * 16, x1 * 16) + 0.5
+        py = np.arange(y0 * 16, y1 * 16) + 0.5
+        dx = m[g, 0] - px[None, :]
+        dy = m[g, 1] - py[:, None]
+        a = ac[g] * np.exp(-0.5 * (con[g, 0] * dx * dx + 2 * con[g, 1] * dx * dy + con[g, 2] * dy * dy))
+        yy, xx = np.nonzero(a >= 1.0 / 255.0)
+        tx, ty = (px[xx] // 16).astype(int), (py[yy] // 16).astype(int)
+        assert np.all((r1[g, 0] <= tx) & (tx < r1[g, 1]) & (r1[g, 2] <= ty) & (ty < r1[g, 3])), g
+        checked += len(xx)
+    assert checked > 10000
 
 
 def test_render_lists_sorted_by_depth():
