@@ -75,6 +75,17 @@ def test_plan_rejects_bad_settings(kw):
     assert code == _lib.ERR_INVALID_ARG
 
 
+def test_plan_rejects_unknown_footprint_and_inference_flags():
+    lib = _lib.load()
+    cams = camera_array(synth.ring_cameras(1, 64, 64))
+    for field in ("alpha_footprint", "inference"):
+        st = make_settings()
+        setattr(st, field, 2)
+        plan = _lib.Plan()
+        assert lib.sixdgs_plan_init(10, 3, cams, 1, ctypes.byref(st), 0, ctypes.byref(plan)) == _lib.ERR_INVALID_ARG
+    assert make_settings().alpha_footprint == 1 and make_settings(alpha_footprint=False).alpha_footprint == 0
+
+
 def test_plan_rejects_bad_sizes():
     cams = synth.ring_cameras(1, 64, 64)
     assert _plan(cams, sh=4)[0] == _lib.ERR_INVALID_ARG
