@@ -4,15 +4,17 @@
 Workload (the headline configuration): 300,000 6D Gaussians on a noisy unit
 shell with strong position-direction coupling, a ring of 8 cameras at
 800x800, L1 loss against targets rendered from a seed-perturbed copy of the
-scene.  One step = condition_project + bin_sort + raster_fwd (fused L1) +
-raster_bwd for all 8 views, i.e. the whole hot path forward and backward.
+scene.  One step = condition_project + bin_sort + raster_fwd_bwd (forward
+blend, fused L1 loss and backward blend in one kernel) + project_bwd for all
+8 views, i.e. the whole hot path forward and backward.
 
 Arms:
   ours (default)     batched: the 8 views in one launch sequence, replayed
                      as one CUDA graph; also timed: the plain form (the same
                      kernels launched once per view, no graph) and the
                      end-to-end form (host parameters and targets copied in,
-                     gradients and loss copied out, every step).
+                     gradients and loss copied out, every step; the copies of
+                     neighbouring steps overlap on two copy streams).
   --impl reference   the FP64 CPU oracle on a bounded sample of the same
                      workload (CPU host cores).
 
@@ -363,6 +365,27 @@ def measure_inference(flush, reps=10, views=synth.TABLE2_TEST_VIEWS):
             "paper_hardware": "not named in the paper", "scenes": out}
 
 
+def host_copy_rates(dev, nbytes=256 << 20, reps=3):
+    """Pinned host <-> device copy rates (GB/s, best of `reps`), the bound on
+    the end-to-end figure's copies."""
+    host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("h2d", lambda: buf.copy_(host, non_blocking=True)),
+                     ("d2h", lambda: host.copy_(buf, non_blocking=True))):
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = round(nbytes / (best * 1e-3) / 1e9, 1)
+    return out
+
+
 def measure_alu_peaks(reps=5):
     """Achieved FP32 FMA (TFLOP/s) and MUFU ex2 (Tops/s) rates of the library's
     saturating probe kernels, best of `reps`, at the GPU's current clocks."""
@@ -681,7 +704,8 @@ def run_ours(args, world, rank, local):
                        "overlap step k's compute (two copy streams, double-buffered staging); the working "
                        "set is larger than L2",
                "sequential": {"value": V * 1000.0 / ms_seq * world, "ms_per_step": ms_seq,
-                              "l2": "flushed between steps"}}
+                              "l2": "flushed between steps"},
+               "host_copy_gbs": host_copy_rates(dev)}
 
     # ---- roofline of the dominant kernel ----
     rc = sx.Renderer(w.scene.n, w.scene.sh_degree, cams, count_pairs=True, **kw)
