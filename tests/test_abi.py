@@ -159,3 +159,13 @@ def test_inference_plan_has_no_gradient_section():
                                  fake, fake, fake, fake, None, 0, None, None) == _lib.ERR_INVALID_ARG
     assert lib.sixdgs_project_bwd(ctypes.byref(inf), ctypes.byref(sc), fake, inf.ws_bytes, fake, fake, fake,
                                   fake, fake, None, 0, None, None) == _lib.ERR_INVALID_ARG
+
+
+def test_header_constants_match_the_binding():
+    text = open(os.path.join(ROOT, "include", "sixdgs.h")).read()
+    defs = dict(re.findall(r"#define\s+(SIXDGS_[A-Z_]+)\s+(.+)", text))
+    assert int(defs["SIXDGS_COND_CACHE_PLANES"]) == _lib.COND_CACHE_PLANES
+    assert eval(defs["SIXDGS_STATIC_WS_BYTES"].replace("u", "")) == _lib.STATIC_WS_BYTES
+    enums = dict((k, int(v)) for k, v in re.findall(r"(SIXDGS_ERR_[A-Z_]+)\s*=\s*(\d+)", text))
+    for name, value in enums.items():
+        assert getattr(_lib, name.replace("SIXDGS_", "")) == value, name
