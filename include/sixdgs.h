@@ -384,8 +384,8 @@ sixdgs_status sixdgs_scale_rotation(int64_t n, const float* l_raw_dev, float* ro
  *
  * Limits: the frame's plan (sixdgs_plan_init with the default duplicate
  * capacity) must need at most SIXDGS_STATIC_WS_BYTES of workspace, about
- * 170,000 (camera, Gaussian) pairs (e.g. 170,624 Gaussians seen by one
- * 800x800 camera, or 42,672 Gaussians by four 256x256 cameras); larger
+ * 170,000 (camera, Gaussian) pairs (e.g. 170,613 Gaussians seen by one
+ * 800x800 camera, or 42,668 Gaussians by four 256x256 cameras); larger
  * frames are refused with SIXDGS_ERR_WORKSPACE before anything is launched.  The array is
  * shared by all calls on a device and keeps the last call's contents (each
  * call clears what it needs); calls that overlap on the GPU (different

@@ -181,6 +181,6 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 12;
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kEmitChunk = 2048;   // duplicates written per expansion chunk
+constexpr int kEmitChunk = 512;    // duplicates written per expansion chunk
 
 }  // namespace sixdgs
