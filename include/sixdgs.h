@@ -267,6 +267,8 @@ sixdgs_status sixdgs_raster_fwd(const sixdgs_plan* plan, void* ws_dev, size_t ws
  * images_dev: written; targets_dev: required; grad_images_dev: optional
  * (NULL: dL/dC is not stored); loss_dev: required, accumulated as in
  * raster_fwd.  Follow with sixdgs_project_bwd for the parameter gradients.
+ * The per-pair gradient records it accumulates are zeroed by
+ * condition_project, so call it (or blend_bwd) once per condition_project.
  * Errors: INVALID_ARG (also for an inference plan), WORKSPACE, CUDA. */
 sixdgs_status sixdgs_raster_fwd_bwd(const sixdgs_plan* plan, void* ws_dev, size_t ws_bytes,
                                     float* images_dev, const float* targets_dev,
