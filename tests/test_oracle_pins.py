@@ -229,6 +229,62 @@ def test_single_gaussian_footprint(s, depth, logit):
             assert abs(img[0, py, px] - exp_val) < 1e-12, (px, py)
 
 
+@pytest.mark.parametrize("l21,l10,logit", [(0.6, 0.0, 1.5), (-0.7, 0.02, 3.0), (0.45, -0.03, 0.0)])
+def test_rotated_anisotropic_footprint(l21, l10, logit):
+    """One Gaussian on the optical axis whose conditional covariance is
+    anisotropic and tilted in the image plane, so that the conic's cross term
+    is large.  Its image must be the 3DGS blend of one entry (section 4.4)
+    with alpha(pixel) = min(0.99, alpha_cond N(x; m, S2) / N(m; m, S2)), the
+    Gaussian ratio taken from scipy's bivariate normal density with
+    S2 = (f/z)^2 (R Sigma_cond R^T)_xy + 0.3 I, and its extent the 3-sigma
+    square of the largest eigenvalue of S2 (numpy).  A sign or factor slip in
+    the cross term of the quadratic form mirrors or reshapes the ellipse."""
+    from scipy.stats import multivariate_normal
+
+    cam = synth.look_at_camera((4.0, 0.0, 0.0), 64, 64)
+    scene = _single_gaussian_scene(0.05, (0.0, 0.0, 0.0), logit, 0.4)
+    # position block of L: rows/cols (x, y, z) of the world; camera x = world
+    # +y, camera y = world -z, so the (y, z) block sets the image ellipse
+    scene.l_raw[1, 0] = math.log(0.06)      # L_yy
+    scene.l_raw[2, 0] = math.log(0.015)     # L_zz
+    k21 = synth.OFFDIAG_ORDER.index((2, 1))
+    k10 = synth.OFFDIAG_ORDER.index((1, 0))
+    scene.l_raw[6 + k21, 0] = 2.0 * math.atanh(l21)
+    scene.l_raw[6 + k10, 0] = 2.0 * math.atanh(l10)
+    st = O.Settings(tile_w=16, tile_h=16, lambda_opa=0.35)
+    img = O.render_view(scene, cam, st)[0].numpy()
+    # Sigma_p from the float32-stored raw values: exp on the diagonal,
+    # 2 sigmoid - 1 below it (Sigma_pd = 0, so Sigma_cond = Sigma_p)
+    raw = scene.l_raw[:, 0].astype(np.float64)
+    Lp = np.diag(np.exp(raw[:3]))
+    for k, (i, j) in enumerate(synth.OFFDIAG_ORDER):
+        if i < 3:
+            Lp[i, j] = 2.0 / (1.0 + math.exp(-raw[6 + k])) - 1.0
+    S = Lp @ Lp.T
+    R = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, -1.0]])    # world -> camera x, y rows
+    f, z = cam.fx, 4.0
+    S2 = (f / z) ** 2 * (R @ S @ R.T) + 0.3 * np.eye(2)
+    assert abs(S2[0, 1]) > 0.3 * math.sqrt(S2[0, 0] * S2[1, 1])   # strongly tilted
+    m = np.array([32.0, 32.0])
+    mvn = multivariate_normal(mean=m, cov=S2)
+    alpha_cond = 1.0 / (1.0 + math.exp(-float(scene.opacity_logit[0])))
+    rgb = 1.0 / (1.0 + math.exp(-float(scene.sh[0, 0]) * 0.5 / math.sqrt(math.pi)))
+    r = 3.0 * math.sqrt(np.linalg.eigvalsh(S2).max())
+    t0, t1 = math.floor((32 - r) / 16), math.floor((32 + r) / 16) + 1
+    ys, xs = np.mgrid[0:64, 0:64]
+    pts = np.stack([xs.ravel() + 0.5, ys.ravel() + 0.5], 1)
+    ratio = (mvn.pdf(pts) / mvn.pdf(m)).reshape(64, 64)
+    a = np.minimum(0.99, alpha_cond * ratio)
+    inside = (t0 <= xs // 16) & (xs // 16 < t1) & (t0 <= ys // 16) & (ys // 16 < t1)
+    expect = np.where(inside & (a >= 1 / 255), a * rgb + (1 - a), 1.0)
+    assert (expect < 1.0).sum() > 40
+    np.testing.assert_allclose(img[0], expect, rtol=0, atol=1e-12)
+    # the mirrored ellipse (cross term of the other sign) is far away
+    mirror = multivariate_normal(mean=m, cov=S2 * np.array([[1, -1], [-1, 1]]))
+    a_m = np.minimum(0.99, alpha_cond * (mirror.pdf(pts) / mirror.pdf(m)).reshape(64, 64))
+    assert np.abs(a_m - a).max() > 0.05
+
+
 def test_off_axis_jacobian():
     """Gaussian off the optical axis: Sigma_2D = s^2 J J^T + 0.3 I with
     J = [[f/z, 0, -f x/z^2], [0, f/z, -f y/z^2]] (no guard clamp hit)."""
