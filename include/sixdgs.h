@@ -9,7 +9,9 @@
  *                       4.2) and EWA-project it to a 2D conic (the 3DGS step
  *                       that section 4.4 keeps unchanged);
  *   bin_sort          : duplicate every visible Gaussian into the screen tiles
- *                       its 3-sigma box touches and radix-sort the
+ *                       of its tile rectangle (settings.alpha_footprint: the
+ *                       3-sigma square, by default intersected with the box
+ *                       of its alpha >= 1/255 ellipse) and radix-sort the
  *                       (tile, depth) keys (section 4.4, inherited 3DGS step);
  *   raster_fwd        : blend every tile front to back (section 4.4), with an
  *                       optional fused L1 loss (the 3DGS loss section 4.4
@@ -223,7 +225,9 @@ size_t sixdgs_workspace_size(const sixdgs_plan* plan);
  * Schur complement Sigma_cond = Sigma_p - A Sigma_pd^T, computed once; then
  * for every camera: d = normalize(mu_p - campos), mu_cond = mu_p +
  * A (d - mu_d), D = (d-mu_d)^T Sigma_d^-1 (d-mu_d), alpha_cond =
- * sigmoid(logit) exp(-lambda_opa D), colour, EWA conic, 3-sigma tile rect.
+ * sigmoid(logit) exp(-lambda_opa D), colour, EWA conic and the tile rect
+ * (the 3-sigma square, intersected with the alpha >= 1/255 box when
+ * settings.alpha_footprint = 1).
  * cams: host array of plan->n_cams cameras; their values are copied into the
  * workspace through kernel parameters (and so into a captured graph).
  * Errors: INVALID_ARG, WORKSPACE, CUDA; device: NONFINITE. */
@@ -384,10 +388,12 @@ sixdgs_status sixdgs_scale_rotation(int64_t n, const float* l_raw_dev, float* ro
  * holds that array until the process exits.  The call allocates nothing
  * (no cudaMalloc, cudaFree or allocating library routine).
  *
- * Limits: the frame's plan (sixdgs_plan_init with the default duplicate
- * capacity) must need at most SIXDGS_STATIC_WS_BYTES of workspace, about
- * 170,000 (camera, Gaussian) pairs (e.g. 170,613 Gaussians seen by one
- * 800x800 camera, or 42,668 Gaussians by four 256x256 cameras); larger
+ * Limits: the frame is planned forward-only whatever the caller's settings
+ * say (as with settings.inference = 1 and store_aux = 0: no gradient
+ * records, no per-pixel walk lengths) with the default duplicate capacity,
+ * and that plan must need at most SIXDGS_STATIC_WS_BYTES of workspace, about
+ * 225,000 (camera, Gaussian) pairs (e.g. 225,925 Gaussians seen by one
+ * 800x800 camera, or 56,504 Gaussians by four 256x256 cameras); larger
  * frames are refused with SIXDGS_ERR_WORKSPACE before anything is launched.  The array is
  * shared by all calls on a device and keeps the last call's contents (each
  * call clears what it needs); calls that overlap on the GPU (different

@@ -44,8 +44,13 @@ extern "C" sixdgs_status sixdgs_render_fwd_static(int64_t n, int32_t sh_degree, 
                                                   const sixdgs_settings* settings, float* images_dev,
                                                   int32_t* status_dev, sixdgs_stream_t stream) {
   if (!scene || !cams || !settings || !images_dev) return SIXDGS_ERR_INVALID_ARG;
+  // A forward-only frame: plan it as one (no gradient-record section, no
+  // per-pixel walk lengths), so the fixed array holds as many pairs as it can.
+  sixdgs_settings fwd = *settings;
+  fwd.inference = 1;
+  fwd.store_aux = 0;
   sixdgs_plan plan;
-  sixdgs_status e = sixdgs_plan_init(n, sh_degree, cams, n_cams, settings, 0, &plan);
+  sixdgs_status e = sixdgs_plan_init(n, sh_degree, cams, n_cams, &fwd, 0, &plan);
   if (e != SIXDGS_OK) return e;
   if (plan.ws_bytes > (int64_t)SIXDGS_STATIC_WS_BYTES) return SIXDGS_ERR_WORKSPACE;
   void* ws = nullptr;

@@ -178,3 +178,27 @@ def assert_within(err, bound, what=""):
         i = np.unravel_index(np.argmax(np.where(bad, err / np.maximum(bound, 1e-300), -np.inf)), err.shape)
         raise AssertionError(f"{what}: {int(bad.sum())} of {err.size} above bound; worst at {i}: "
                              f"{err[i]:.3e} vs {bound[i]:.3e}")
+
+
+def validate_image(img_gpu, ref, prep, cam, st):
+    """Whole-image check of a GPU render (3, H, W) against the oracle's
+    full image ``ref``: every pixel within IMAGE_TOL, except pixels whose
+    value the oracle reproduces (within IMAGE_TOL) under a borderline
+    decision flip (tile membership, depth order, skip or stop).  Returns the
+    mask (H, W) of those borderline pixels and the largest plain error."""
+    img_gpu = np.asarray(img_gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    err = np.abs(img_gpu - ref).max(axis=0)
+    over = err > IMAGE_TOL
+    border = np.zeros_like(over)
+    if over.any():
+        cert, poss, sure, maybe = membership_sets(prep, cam, st)
+        ys, xs = np.nonzero(over)
+        for (x, y) in sorted({(int(x) // st.tile_w, int(y) // st.tile_h) for x, y in zip(xs, ys)}):
+            certain, possible = tile_membership(cert, poss, sure, maybe, x, y)
+            x0, y0 = x * st.tile_w, y * st.tile_h
+            block = img_gpu[:, y0:y0 + st.tile_h, x0:x0 + st.tile_w]
+            e = compare_tile_image(block, prep, cam, st, x, y, certain, possible).max(axis=0)
+            assert_within(e, IMAGE_TOL, f"tile ({x}, {y})")
+            border[y0:y0 + st.tile_h, x0:x0 + st.tile_w] |= over[y0:y0 + st.tile_h, x0:x0 + st.tile_w]
+    return border, float(err[~over].max()) if (~over).any() else 0.0

@@ -40,8 +40,26 @@ def test_launches_per_frame_counts_the_step_kernels():
     assert bench.launches_per_frame(plan, 8) == 1 + 1 + 1 + 4 + 2 + 2 + 1 + 1 + 1 + 1
 
 
-def test_oracle_baseline_on_a_small_sample():
+def test_oracle_baseline_times_whole_views_with_all_and_one_thread():
     w = synth.make_workload(0)
-    r = bench.oracle_baseline(w, samples=1, sample_tiles=4)
+    r = bench.oracle_baseline(w)
     assert r["kind"] == "oracle" and r["unit"] == bench.UNIT and r["value"] > 0 and r["cores"] >= 1
-    assert "4 occupied 16x16 tiles" in r["sample"]
+    assert r["sample"].startswith("2 whole views") and r["cpu_model"]
+    st = r["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0
+
+
+def test_reference_arm_line_matches_the_workload_config(capsys):
+    """The reference arm prints one line per the contract, with the same
+    config as the GPU arm's and one whole view per step."""
+    import argparse
+    import json
+
+    args = argparse.Namespace(config=0, n=0, steps=1, warmup=0)
+    bench.run_reference(args, 1, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["steps"] == 1
+    w = synth.make_workload(0)
+    assert line["config"] == bench.workload_config(w, (16, 16), 1)
+    assert abs(line["ms_per_step"] - 1000.0 / line["value"]) < 0.02 * line["ms_per_step"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

@@ -56,19 +56,27 @@ def test_capacity_overflow_is_reported_then_regrown():
 
 
 def test_lookback_budget_expiry_is_reported_and_context_survives():
+    """A one-cycle spin budget: the first look-back of a scan or sort tile
+    that finds its predecessor not yet published gives up at once, so with
+    the hundreds of concurrent tiles of the 200k-Gaussian frame the timeout
+    must be reported (it is checked, not assumed).  The kernels return
+    instead of waiting, every write stays in bounds, and the context keeps
+    working: the next normal frame is exact."""
     w = synth.make_workload(1)
     params = sx.params_to_device(w.scene)
-    r = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, spin_budget=1)
-    img = r.forward(params, check=False)
-    torch.cuda.synchronize()
-    st = int(r.status.item())
-    assert st & ~TIMEOUT == 0, _lib.status_names(st)
     ref = _reference(w.scene, w.cameras)
-    if st == 0:      # no block ever had to wait: the result must then be exact
-        torch.testing.assert_close(img, ref, rtol=0, atol=0)
-    else:
-        print("look-back budget expired and was reported")
-    # the context is intact: a normal frame on the same renderer's GPU
+    r = sx.Renderer(w.scene.n, w.scene.sh_degree, w.cameras, spin_budget=1)
+    seen = []
+    for _ in range(4):
+        r.forward(params, check=False)
+        torch.cuda.synchronize()
+        st = int(r.status.item())
+        assert st & ~TIMEOUT == 0, _lib.status_names(st)
+        seen.append(st)
+        if st & TIMEOUT:
+            break
+    assert any(s & TIMEOUT for s in seen), seen
+    # the context is intact: a normal frame on the same GPU
     torch.testing.assert_close(_reference(w.scene, w.cameras), ref, rtol=0, atol=0)
 
 

@@ -79,10 +79,51 @@ def test_static_workspace_render_matches_staged_calls_twice_in_a_row():
 
 
 def test_static_workspace_refuses_frames_beyond_its_size():
-    scene = synth.scene_shell(200_000, 3)
+    scene = synth.scene_shell(240_000, 3)
     cams = [synth.look_at_camera((4.0, 0.0, 0.0), 800, 800)]
-    plan = sx.make_plan(scene.n, scene.sh_degree, cams, make_settings())
+    plan = sx.make_plan(scene.n, scene.sh_degree, cams, make_settings(inference=True))
     assert plan.ws_bytes > _lib.STATIC_WS_BYTES
     code, images, status = _static_render(scene, cams, make_settings())
     assert code == _lib.ERR_WORKSPACE
     assert torch.all(images == -1.0)          # nothing was launched
+
+
+def test_static_workspace_fits_a_forward_only_frame_of_200k_gaussians():
+    """The frame is planned forward-only (no gradient records), so 200,000
+    Gaussians at 800x800 fit although a training plan of that frame would not."""
+    scene = synth.scene_shell(200_000, 3)
+    cams = [synth.look_at_camera((4.0, 0.0, 0.0), 800, 800)]
+    assert sx.make_plan(scene.n, scene.sh_degree, cams, make_settings()).ws_bytes > _lib.STATIC_WS_BYTES
+    settings = make_settings()
+    code, got, status = _static_render(scene, cams, settings)
+    assert code == _lib.OK and status == 0
+    err = float((got - _staged_render(scene, cams)).abs().max())
+    assert err <= IMAGE_TOL, err
+
+
+def test_static_workspace_call_allocates_nothing():
+    """After a first call (which looks up the array's address and loads the
+    library's kernels), a call changes neither the device's free memory nor
+    what PyTorch's allocator holds."""
+    a = synth.make_workload(0)
+    lib = _lib.load()
+    params = sx.params_to_device(a.scene)
+    images = torch.empty(3 * 128 * 128, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sc = _scene_struct(params, a.scene.n, a.scene.sh_degree)
+    cams = camera_array(a.cameras)
+    settings = make_settings()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        code = lib.sixdgs_render_fwd_static(a.scene.n, a.scene.sh_degree, ctypes.byref(sc), cams, 1,
+                                            ctypes.byref(settings), ctypes.c_void_p(images.data_ptr()),
+                                            ctypes.c_void_p(status.data_ptr()), stream)
+        torch.cuda.synchronize()
+        assert code == _lib.OK and int(status.item()) == 0
+
+    call()
+    free0, held0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    call()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == held0
