@@ -240,36 +240,90 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, 
   }
 }
 
-// Sum of 8 per-lane values over the warp with 9 shuffles instead of 40:
-// each butterfly step sends half of the values a lane still carries to its
-// partner and keeps the other half, so after the xor-16/8/4 steps lane l
-// carries only value 4*b4 + 2*b3 + b2 (bits of l), summed over the lanes
-// that differ in those bits, and the xor-2/1 steps finish the sum.  Returns
-// the total of that value; its index is (l >> 2) & 7.
-__device__ __forceinline__ float warp_sum8_transposed(const float* v, int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-  float h[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float keep = b4 ? v[i + 4] : v[i];
-    const float send = b4 ? v[i] : v[i + 4];
-    h[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  float q[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float keep = b3 ? h[i + 2] : h[i];
-    const float send = b3 ? h[i] : h[i + 2];
-    q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  float r = (b2 ? q[1] : q[0]) + __shfl_xor_sync(0xffffffffu, b2 ? q[0] : q[1], 4);
-  r += __shfl_xor_sync(0xffffffffu, r, 2);
-  r += __shfl_xor_sync(0xffffffffu, r, 1);
-  return r;
-}
-
 __device__ __forceinline__ void red_add(float* addr, float x) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
+}
+
+// The backward walk runs in two passes per warp so that no value has to be
+// summed across the lanes of a warp for every list entry:
+//  1. pixel-parallel (lane = pixel), front to back like the forward: the
+//     transmittance T and the running dL/dC . (colour prefix) Q are carried
+//     per pixel, and each pixel's dL/dq and blend weight w for the entry are
+//     written to the warp's shared-memory slots (kSlots entries at a time);
+//  2. entry-parallel, once kSlots entries are buffered (or the batch ends):
+//     the warp splits into 32 / kSlots groups of kSlots lanes, lane s of a
+//     group takes slot s and sums its nine record gradients over the group's
+//     kSlots pixels in registers; the groups are added with shuffles and
+//     lane s of the first group adds the entry's sums to the record
+//     gradients in global memory.
+// Pass 2 reads what pass 1 stored for a slot at pixel p from index p ^ s, so
+// the row writes of pass 1 and the column reads of pass 2 are both free of
+// shared-memory bank conflicts.
+#ifndef SIXDGS_BWD_SLOTS
+#define SIXDGS_BWD_SLOTS 8
+#endif
+constexpr int kSlots = SIXDGS_BWD_SLOTS;
+static_assert(kSlots == 8 || kSlots == 16, "slots per warp: 8 or 16");
+struct __align__(16) WarpScratch {
+  float2 dqw[kSlots][32];   // (dL/dq / ln 2, w) of slot s at pixel p, at [s][p ^ s]
+  float4 pix[35];           // dL/dC of pixel p at p + (p >> 3) (groups in other banks)
+  int slot_j[kSlots];       // batch index of the entry in slot s
+};
+
+__host__ __device__ constexpr int bwd_scratch_bytes(int threads) {
+  return (threads / 32) * (int)sizeof(WarpScratch);
+}
+
+// Pass 2 over slots [0, k).  x0, y0: centre of the sub-block's first pixel.
+__device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws, int k, const float4* s_a,
+                                            const float4* s_c, float x0, float y0) {
+  constexpr int kRowsPerGroup = kSlots / kSubW;
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  const int s = lane & (kSlots - 1);
+  const int grp = lane / kSlots;
+  const bool active = s < k;
+  const int j = ws.slot_j[s];
+  float ux = 0.f, vy = 0.f;
+  if (active) {
+    const float4 ra = s_a[j];
+    ux = ra.x - x0;                                   // dx at column c is ux - c
+    vy = ra.y - y0 - (float)(grp * kRowsPerGroup);    // dy at row r of the group is vy - r
+  }
+  float g[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) g[q] = 0.f;
+  const float2* row = ws.dqw[s];
+#pragma unroll
+  for (int i = 0; i < kSlots; ++i) {
+    const int p = grp * kSlots + i;
+    const float2 v = row[p ^ s];
+    const float4 dc = ws.pix[p + (p >> 3)];
+    const float dx = ux - (float)(i & (kSubW - 1));
+    const float dy = vy - (float)(i / kSubW);
+    const float dq = v.x, w = v.y;
+    g[0] = fmaf(dq, dx, g[0]);
+    g[1] = fmaf(dq, dy, g[1]);
+    const float mx = dq * dx, my = dq * dy;
+    g[2] = fmaf(mx, dx, g[2]);
+    g[3] = fmaf(mx, dy, g[3]);
+    g[4] = fmaf(my, dy, g[4]);
+    g[5] += dq;
+    g[6] = fmaf(dc.x, w, g[6]);
+    g[7] = fmaf(dc.y, w, g[7]);
+    g[8] = fmaf(dc.z, w, g[8]);
+  }
+#pragma unroll
+  for (int o = kSlots; o < 32; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) g[q] += __shfl_xor_sync(0xffffffffu, g[q], o);
+  if (active && grp == 0) {
+    float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      if (g[q] != 0.f) red_add(dst + q, g[q]);
+  }
+  __syncwarp();
 }
 
 // Backward replay of a tile's list for the calling thread's pixel, front to
@@ -280,7 +334,8 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
 template <bool kRecompute>
 __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
                                          uint2 range, bool inside, const float* Cf, const float* dC,
-                                         uint32_t bound, bool staged, float4* s_a, float4* s_b, float4* s_c) {
+                                         uint32_t bound, bool staged, float4* s_a, float4* s_b, float4* s_c,
+                                         WarpScratch& ws) {
   const int B = a.batch;
   const int lane = threadIdx.x & 31;
   // dL/dalpha_i = sum_c dC_c (c_i T_i - S_c / (1 - alpha_i)) with S the colour
@@ -289,6 +344,9 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
   const float D0 = dC[0] * Cf[0] + dC[1] * Cf[1] + dC[2] * Cf[2];
   float T = 1.f, Q = 0.f;
   bool done = !inside;
+  if (kRecompute || !inside) bound = inside ? 0xffffffffu : 0u;   // outside the image: an empty walk
+  ws.pix[lane + (lane >> 3)] = make_float4(dC[0], dC[1], dC[2], 0.f);
+  int k = 0;          // slots filled (warp-uniform)
 
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
@@ -296,6 +354,8 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
     if (!staged) load_batch(a, start, cnt, s_a, s_b, s_c);
     __syncthreads();
     if (__all_sync(0xffffffffu, done)) continue;
+    // entries j < lim of this batch lie within the pixel's walk
+    const int lim = (int)min((uint32_t)cnt, bound - min(bound, start - range.x));
     for (int base = 0; base < cnt; base += 32) {
       const int jl = base + lane;
       const bool rel = jl < cnt && reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl]);
@@ -305,58 +365,41 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
         mask &= mask - 1;
         // Branch-free, as in the forward: alpha = 0 for a pixel that skips
         // the entry or is finished, which leaves T and Q unchanged and gives
-        // zero gradient.
+        // zero dq and w.
         const float4 ra = s_a[j], rb = s_b[j];
         const float blue = s_c[j].x;
-        if (!kRecompute) done = done || (start - range.x + j >= bound);
         float dx, dy;
         const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
-        const bool vis = !done && q >= kQMin;
+        const bool vis = (kRecompute ? !done : j < lim) && q >= kQMin;
         const float e = ex2_approx(q);
         const float alpha = vis ? fminf(kAlphaMax, e) : 0.f;
-        const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        const float om = __fsub_rn(1.f, alpha);
+        const float test_T = __fmul_rn(T, om);
+        // stored walk: never a stop inside it, and alpha = 0 past it
         const bool stop = kRecompute && test_T < kTMin;
-        const bool contrib = vis && !stop;
-        const float w = contrib ? __fmul_rn(alpha, T) : 0.f;
+        const float w = stop ? 0.f : __fmul_rn(alpha, T);
         const float G = dC[0] * rb.z + dC[1] * rb.w + dC[2] * blue;
         Q = fmaf(w, G, Q);   // now includes this entry: D0 - Q is behind it
-        const float dLda = T * G - (D0 - Q) * __fdividef(1.f, 1.f - alpha);
+        const float dLda = T * G - (D0 - Q) * __fdividef(1.f, om);
         // dL/dq / ln 2 (the factor ln 2 of d 2^q / dq is applied by the
-        // per-Gaussian backward); no gradient through the 0.99 clamp
-        const float dq = (contrib && e <= kAlphaMax) ? dLda * alpha : 0.f;
-        const float mx = dq * dx, my = dq * dy;
-        float g[9];
-        g[0] = mx;
-        g[1] = my;
-        g[2] = mx * dx;
-        g[3] = mx * dy;
-        g[4] = my * dy;
-        g[5] = dq;
-        g[6] = dC[0] * w;
-        g[7] = dC[1] * w;
-        g[8] = dC[2] * w;
-        T = contrib ? test_T : T;
-        done = done || stop;
-        const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
-        if (cmask) {
-          float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
-          // Few pixels: their own 9 atomics each (one warp instruction per
-          // value whatever the number of lanes) beat the warp reduction; the
-          // threshold 4 was the fastest of 1, 2, 4, 8 and 32.
-          if (__popc(cmask) <= 4) {
-            if (contrib) {
-#pragma unroll
-              for (int k = 0; k < 9; ++k) red_add(dst + k, g[k]);
-            }
-          } else {
-            const float s8 = warp_sum8_transposed(g, lane);
-            const float s9 = warp_sum(g[8]);
-            if ((lane & 3) == 0) red_add(dst + ((lane >> 2) & 7), s8);
-            if (lane == 0) red_add(dst + 8, s9);
-          }
+        // per-Gaussian backward); no gradient through the 0.99 clamp; alpha = 0
+        // (skipped, off the walk) gives dq = 0
+        const float dq = (!stop && e <= kAlphaMax) ? dLda * alpha : 0.f;
+        T = stop ? T : test_T;
+        if (kRecompute) done = done || stop;
+        ws.dqw[k][lane ^ k] = make_float2(dq, w);
+        if (lane == 0) ws.slot_j[k] = j;
+        if (++k == kSlots) {
+          flush_slots(a, ws, k, s_a, s_c, pm.x0, pm.y0);
+          k = 0;
         }
       }
-      if (__all_sync(0xffffffffu, done)) break;
+      if (__all_sync(0xffffffffu, kRecompute ? done : base + 32 >= lim)) break;
+    }
+    if (!kRecompute) done = done || start - range.x + cnt >= bound;
+    if (k) {   // the slots refer to this batch's shared-memory records
+      flush_slots(a, ws, k, s_a, s_c, pm.x0, pm.y0);
+      k = 0;
     }
   }
 }
@@ -389,7 +432,9 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
     }
     if (!kRecompute) bound = a.nwalk[cam.pixel_base + pix];
   }
-  bwd_walk<kRecompute>(a, pm, pxc, pyc, range, inside, Cf, dC, bound, false, s_mem, s_mem + B, s_mem + 2 * B);
+  WarpScratch* ws = reinterpret_cast<WarpScratch*>(s_mem + 3 * B);
+  bwd_walk<kRecompute>(a, pm, pxc, pyc, range, inside, Cf, dC, bound, false, s_mem, s_mem + B, s_mem + 2 * B,
+                       ws[threadIdx.x >> 5]);
 }
 
 // Forward blend, fused L1 loss and backward blend of global tile gt by the
@@ -450,13 +495,20 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += s_red[w];
     atomicAdd(a.loss, sum * (double)a.inv_count);
   }
-  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_a, s_b, s_c);
+  WarpScratch* ws = reinterpret_cast<WarpScratch*>(s_mem + 3 * B);
+  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_a, s_b, s_c,
+                  ws[threadIdx.x >> 5]);
 }
 
-// 40 registers (6 CTAs of 256 threads per SM, as the separate kernels): with
-// only a 512-thread bound the compiler picks 40 and spills 44 bytes; capped
-// explicitly it spills 8 and ran 1-2% faster than both that and 48 or 70.
-__global__ void __maxnreg__(40) blend_fused_kernel(BlendArgs a) {
+// Register budgets of the kernels that run the backward walk (swept on the
+// 300k / 8 x 800^2 frame).
+#ifndef SIXDGS_FUSED_MAXNREG
+#define SIXDGS_FUSED_MAXNREG 64
+#endif
+#ifndef SIXDGS_BWD_MAXNREG
+#define SIXDGS_BWD_MAXNREG 48
+#endif
+__global__ void __maxnreg__(SIXDGS_FUSED_MAXNREG) blend_fused_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
   if (!a.tile_queue) {
     blend_fused_tile(a, blockIdx.x, s_mem);
@@ -495,7 +547,7 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(BlendArgs a) {
 }
 
 template <bool kRecompute>
-__global__ void __launch_bounds__(512) blend_bwd_kernel(BlendArgs a) {
+__global__ void __maxnreg__(SIXDGS_BWD_MAXNREG) blend_bwd_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
   if (!a.tile_queue) {
     blend_bwd_tile<kRecompute>(a, blockIdx.x, s_mem);
@@ -530,10 +582,11 @@ static int resident_grid(const void* fn, int threads, int smem, int64_t tiles) {
   return (int)std::min<int64_t>(g, tiles);
 }
 
+// scratch: the backward walk's per-warp shared memory (0 for the forward)
 template <typename K>
-static void launch_blend(K kernel, const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
-  const int smem = blend_smem(a.batch);
+static void launch_blend(K kernel, const BlendArgs& a, int64_t total_tiles, bool scratch, cudaStream_t stream) {
   const int threads = a.tile_w * a.tile_h;
+  const int smem = blend_smem(a.batch) + (scratch ? bwd_scratch_bytes(threads) : 0);
   allow_smem((const void*)kernel, smem);
   if (a.tile_queue) {
     cudaMemsetAsync(a.tile_queue, 0, sizeof(uint32_t), stream);
@@ -547,23 +600,23 @@ static void launch_blend(K kernel, const BlendArgs& a, int64_t total_tiles, cuda
 void launch_blend_fwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
   if (a.pair_counts) {
-    if (a.nwalk) launch_blend(blend_fwd_kernel<true, true>, a, total_tiles, stream);
-    else launch_blend(blend_fwd_kernel<true, false>, a, total_tiles, stream);
+    if (a.nwalk) launch_blend(blend_fwd_kernel<true, true>, a, total_tiles, false, stream);
+    else launch_blend(blend_fwd_kernel<true, false>, a, total_tiles, false, stream);
   } else {
-    if (a.nwalk) launch_blend(blend_fwd_kernel<false, true>, a, total_tiles, stream);
-    else launch_blend(blend_fwd_kernel<false, false>, a, total_tiles, stream);
+    if (a.nwalk) launch_blend(blend_fwd_kernel<false, true>, a, total_tiles, false, stream);
+    else launch_blend(blend_fwd_kernel<false, false>, a, total_tiles, false, stream);
   }
 }
 
 void launch_blend_fused(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  launch_blend(blend_fused_kernel, a, total_tiles, stream);
+  launch_blend(blend_fused_kernel, a, total_tiles, true, stream);
 }
 
 void launch_blend_bwd(const BlendArgs& a, int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles == 0) return;
-  if (a.recompute) launch_blend(blend_bwd_kernel<true>, a, total_tiles, stream);
-  else launch_blend(blend_bwd_kernel<false>, a, total_tiles, stream);
+  if (a.recompute) launch_blend(blend_bwd_kernel<true>, a, total_tiles, true, stream);
+  else launch_blend(blend_bwd_kernel<false>, a, total_tiles, true, stream);
 }
 
 }  // namespace sixdgs

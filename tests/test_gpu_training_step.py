@@ -128,7 +128,6 @@ def _check_step_against_oracle(w, cams, st, r, res, targets, tag):
     l_ref, _ = O.l1_loss(refs, targets)
     # |L_gpu - L_oracle| <= mean |C_gpu - C_oracle| (triangle inequality) + accumulation rounding
     assert abs(res["loss"] - l_ref) <= diff / M + 1e-6 * l_ref, (res["loss"], l_ref)
-    assert undecided <= 1e-3 * M, undecided
     ref_g = None
     for v, cam in enumerate(cams):
         gv = O.gradients(w.scene, [cam], [gviews[v].astype(np.float64)], st)
