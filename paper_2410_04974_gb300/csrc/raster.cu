@@ -249,24 +249,22 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
 //  1. pixel-parallel (lane = pixel), front to back like the forward: the
 //     transmittance T and the running dL/dC . (colour prefix) Q are carried
 //     per pixel, and each pixel's dL/dq and blend weight w for the entry are
-//     written to the warp's shared-memory slots (kSlots entries at a time);
-//  2. entry-parallel, once kSlots entries are buffered (or the batch ends):
-//     the warp splits into 32 / kSlots groups of kSlots lanes, lane s of a
-//     group takes slot s and sums its nine record gradients over the group's
-//     kSlots pixels in registers; the groups are added with shuffles and
-//     lane s of the first group adds the entry's sums to the record
-//     gradients in global memory.
+//     written to the warp's shared-memory slots (kSlots = 8 entries at a
+//     time);
+//  2. entry-parallel, once the slots are full (or the batch ends): lane
+//     8 r + s takes slot s over row r of the 8 x 4 sub-block and sums, over
+//     the row's 8 pixels, dq, c dq, c^2 dq and dL/dC . w (c the column
+//     relative to the sub-block's centre); the four rows are added with
+//     shuffles, and lane s turns the sums into the entry's nine record
+//     gradients (moments of dq in dx = u - px, dy = v - py) and adds them to
+//     the record gradients in global memory.
 // Pass 2 reads what pass 1 stored for a slot at pixel p from index p ^ s, so
 // the row writes of pass 1 and the column reads of pass 2 are both free of
 // shared-memory bank conflicts.
-#ifndef SIXDGS_BWD_SLOTS
-#define SIXDGS_BWD_SLOTS 8
-#endif
-constexpr int kSlots = SIXDGS_BWD_SLOTS;
-static_assert(kSlots == 8 || kSlots == 16, "slots per warp: 8 or 16");
+constexpr int kSlots = 8;
 struct __align__(16) WarpScratch {
   float2 dqw[kSlots][32];   // (dL/dq / ln 2, w) of slot s at pixel p, at [s][p ^ s]
-  float4 pix[35];           // dL/dC of pixel p at p + (p >> 3) (groups in other banks)
+  float4 pix[35];           // dL/dC of pixel p at p + (p >> 3) (rows in other banks)
   int slot_j[kSlots];       // batch index of the entry in slot s
 };
 
@@ -274,50 +272,49 @@ __host__ __device__ constexpr int bwd_scratch_bytes(int threads) {
   return (threads / 32) * (int)sizeof(WarpScratch);
 }
 
-// Pass 2 over slots [0, k).  x0, y0: centre of the sub-block's first pixel.
+// Pass 2 over slots [0, k).  xc, yc: centre of the 8 x 4 sub-block.
 __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws, int k, const float4* s_a,
-                                            const float4* s_c, float x0, float y0) {
-  constexpr int kRowsPerGroup = kSlots / kSubW;
+                                            const float4* s_c, float xc, float yc) {
+  static_assert(kSlots == kSubW && kSubH == 4, "one row of the sub-block per slot group");
   __syncwarp();
   const int lane = threadIdx.x & 31;
   const int s = lane & (kSlots - 1);
-  const int grp = lane / kSlots;
-  const bool active = s < k;
-  const int j = ws.slot_j[s];
-  float ux = 0.f, vy = 0.f;
-  if (active) {
-    const float4 ra = s_a[j];
-    ux = ra.x - x0;                                   // dx at column c is ux - c
-    vy = ra.y - y0 - (float)(grp * kRowsPerGroup);    // dy at row r of the group is vy - r
-  }
-  float g[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) g[q] = 0.f;
+  const int r = lane >> 3;                 // row of the sub-block
   const float2* row = ws.dqw[s];
+  float R0 = 0.f, R1 = 0.f, R2 = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
 #pragma unroll
-  for (int i = 0; i < kSlots; ++i) {
-    const int p = grp * kSlots + i;
+  for (int c = 0; c < kSubW; ++c) {
+    const int p = r * kSubW + c;
     const float2 v = row[p ^ s];
     const float4 dc = ws.pix[p + (p >> 3)];
-    const float dx = ux - (float)(i & (kSubW - 1));
-    const float dy = vy - (float)(i / kSubW);
-    const float dq = v.x, w = v.y;
-    g[0] = fmaf(dq, dx, g[0]);
-    g[1] = fmaf(dq, dy, g[1]);
-    const float mx = dq * dx, my = dq * dy;
-    g[2] = fmaf(mx, dx, g[2]);
-    g[3] = fmaf(mx, dy, g[3]);
-    g[4] = fmaf(my, dy, g[4]);
-    g[5] += dq;
-    g[6] = fmaf(dc.x, w, g[6]);
-    g[7] = fmaf(dc.y, w, g[7]);
-    g[8] = fmaf(dc.z, w, g[8]);
+    const float cc = (float)c - 0.5f * (float)(kSubW - 1);   // column about the centre
+    R0 += v.x;
+    R1 = fmaf(cc, v.x, R1);
+    R2 = fmaf(cc * cc, v.x, R2);
+    G0 = fmaf(dc.x, v.y, G0);
+    G1 = fmaf(dc.y, v.y, G1);
+    G2 = fmaf(dc.z, v.y, G2);
   }
+  const float rr = (float)r - 0.5f * (float)(kSubH - 1);      // row about the centre
+  // moments of dq in (c, r) about the centre: 1, c, r, c^2, c r, r^2; then dL/dC . w
+  float m[9] = {R0, R1, rr * R0, R2, rr * R1, rr * rr * R0, G0, G1, G2};
 #pragma unroll
   for (int o = kSlots; o < 32; o <<= 1)
 #pragma unroll
-    for (int q = 0; q < 9; ++q) g[q] += __shfl_xor_sync(0xffffffffu, g[q], o);
-  if (active && grp == 0) {
+    for (int q = 0; q < 9; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], o);
+  if (lane < k) {
+    const int j = ws.slot_j[lane];
+    const float U = s_a[j].x - xc, V = s_a[j].y - yc;   // dx = U - c, dy = V - r
+    float g[9];
+    g[0] = fmaf(U, m[0], -m[1]);                          // sum dq dx
+    g[1] = fmaf(V, m[0], -m[2]);                          // sum dq dy
+    g[2] = fmaf(U, fmaf(U, m[0], -2.f * m[1]), m[3]);     // sum dq dx^2
+    g[3] = fmaf(U, fmaf(V, m[0], -m[2]), fmaf(-V, m[1], m[4]));   // sum dq dx dy
+    g[4] = fmaf(V, fmaf(V, m[0], -2.f * m[2]), m[5]);     // sum dq dy^2
+    g[5] = m[0];
+    g[6] = m[6];
+    g[7] = m[7];
+    g[8] = m[8];
     float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
 #pragma unroll
     for (int q = 0; q < 9; ++q)
@@ -390,7 +387,7 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
         ws.dqw[k][lane ^ k] = make_float2(dq, w);
         if (lane == 0) ws.slot_j[k] = j;
         if (++k == kSlots) {
-          flush_slots(a, ws, k, s_a, s_c, pm.x0, pm.y0);
+          flush_slots(a, ws, k, s_a, s_c, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
           k = 0;
         }
       }
@@ -398,7 +395,7 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
     }
     if (!kRecompute) done = done || start - range.x + cnt >= bound;
     if (k) {   // the slots refer to this batch's shared-memory records
-      flush_slots(a, ws, k, s_a, s_c, pm.x0, pm.y0);
+      flush_slots(a, ws, k, s_a, s_c, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
       k = 0;
     }
   }
@@ -506,7 +503,7 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
 #define SIXDGS_FUSED_MAXNREG 64
 #endif
 #ifndef SIXDGS_BWD_MAXNREG
-#define SIXDGS_BWD_MAXNREG 48
+#define SIXDGS_BWD_MAXNREG 64
 #endif
 __global__ void __maxnreg__(SIXDGS_FUSED_MAXNREG) blend_fused_kernel(BlendArgs a) {
   extern __shared__ float4 s_mem[];
