@@ -1,6 +1,7 @@
 // C ABI of the sixdgs library: plan and workspace layout, argument checks
 // and the launch sequence of each stage (declared in include/sixdgs.h).
 #include <cstring>
+#include <initializer_list>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -96,6 +97,16 @@ sixdgs_status check_ws(const sixdgs_plan* p, void* ws, size_t ws_bytes) {
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return SIXDGS_ERR_INVALID_ARG;
   if ((int64_t)ws_bytes < p->ws_bytes) return SIXDGS_ERR_WORKSPACE;
   return SIXDGS_OK;
+}
+
+// Can every plane segment of a staged tile of Gaussians be copied in bulk
+// (16-byte-aligned source, length a multiple of 16 bytes)?  Null pointers
+// (absent planes) do not count.
+bool bulk_planes(int64_t n, std::initializer_list<const float*> arrays) {
+  if (n % 4 != 0) return false;
+  for (const float* p : arrays)
+    if (p && (reinterpret_cast<uintptr_t>(p) & 15u) != 0) return false;
+  return true;
 }
 
 sixdgs_status launch_status() {
@@ -263,6 +274,9 @@ sixdgs_status sixdgs_condition_project(const sixdgs_plan* p, const sixdgs_scene*
   a.rect = ws_ptr<ushort4>(ws, p, SIXDGS_WS_RECT);
   a.depth_key = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_DEPTHKEY);
   a.grad_rec = p->settings.inference ? nullptr : ws_ptr<float>(ws, p, SIXDGS_WS_GRADREC);
+  a.bulk = bulk_planes(p->n, {a.mu_p, a.mu_d, a.sh, a.lambda_raw, a.cond_cache,
+                              a.cond_cache ? nullptr : a.l_raw, a.cond_cache ? nullptr : a.opacity_logit});
+  a.spin_budget = spin_budget(p);
   a.status = status_dev;
   launch_project_fwd(a, stream);
   return launch_status();

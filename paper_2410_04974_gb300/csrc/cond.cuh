@@ -17,14 +17,15 @@ struct CondState {
   float alpha; // sigmoid(opacity logit)
 };
 
-__device__ __forceinline__ void load_cholesky(const float* __restrict__ l_raw, int64_t n, int64_t g,
-                                              float L[6][6]) {
+// L from the 21 raw planes; plane(p) returns raw plane p of this Gaussian.
+template <typename Plane>
+__device__ __forceinline__ void cholesky_from(Plane plane, float L[6][6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < 6; ++j) L[i][j] = 0.f;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) L[i][i] = __expf(__ldg(l_raw + i * n + g));
+  for (int i = 0; i < 6; ++i) L[i][i] = __expf(plane(i));
   int k = 6;
 #pragma unroll
   for (int i = 1; i < 6; ++i)
@@ -34,8 +35,13 @@ __device__ __forceinline__ void load_cholesky(const float* __restrict__ l_raw, i
       // the subtraction form loses the relative accuracy of small entries
       // (|v| ~ 1e-3 keeps only ~3 significant digits in FP32), tanhf keeps
       // it to a few ulps.
-      L[i][j] = tanhf(0.5f * __ldg(l_raw + (k++) * n + g));
+      L[i][j] = tanhf(0.5f * plane(k++));
     }
+}
+
+__device__ __forceinline__ void load_cholesky(const float* __restrict__ l_raw, int64_t n, int64_t g,
+                                              float L[6][6]) {
+  cholesky_from([&](int p) { return __ldg(l_raw + p * n + g); }, L);
 }
 
 // Sigma_p = Lpp Lpp^T, Sigma_pd = Lpp Ldp^T, Sigma_d = Ldp Ldp^T + Ldd Ldd^T.
@@ -57,10 +63,10 @@ __device__ __forceinline__ void sigma_blocks(const float L[6][6], M3& Sp, M3& Sp
     }
 }
 
-__device__ __forceinline__ bool condition_gaussian(const float* __restrict__ l_raw, float logit,
-                                                   int64_t n, int64_t g, CondState& s) {
+template <typename Plane>
+__device__ __forceinline__ bool condition_from(Plane plane, float logit, CondState& s) {
   float L[6][6];
-  load_cholesky(l_raw, n, g, L);
+  cholesky_from(plane, L);
   M3 Sp, Spd, Sd;
   sigma_blocks(L, Sp, Spd, Sd);
   if (!spd_inverse(Sd, s.Sdi)) return false;
@@ -68,6 +74,11 @@ __device__ __forceinline__ bool condition_gaussian(const float* __restrict__ l_r
   s.Sc = sub(Sp, mul_bt(s.A, Spd));
   s.alpha = sigmoidf_(logit);
   return true;
+}
+
+__device__ __forceinline__ bool condition_gaussian(const float* __restrict__ l_raw, float logit,
+                                                   int64_t n, int64_t g, CondState& s) {
+  return condition_from([&](int p) { return __ldg(l_raw + p * n + g); }, logit, s);
 }
 
 }  // namespace sixdgs

@@ -25,6 +25,8 @@ struct ProjectArgs {
   ushort4* rect;
   uint32_t* depth_key;
   float* grad_rec;   // zeroed for every visible pair (read by the backward); null: inference plan
+  int32_t bulk;      // 1: every parameter plane segment can be staged with bulk copies
+  int64_t spin_budget;
   int32_t* status;
 };
 

@@ -252,3 +252,23 @@ def test_plain_three_sigma_footprint_and_equal_images():
     assert torch.equal(img0, img1)
     k0, k1 = int(r0.counts()[1]), int(r1.counts()[1])
     assert k1 < 0.85 * k0, (k0, k1)
+
+
+def test_plane_length_not_a_multiple_of_four():
+    """4,099 Gaussians: the parameter planes cannot be staged with 16-byte
+    bulk copies, so the projection loads them with plain loads; records,
+    lists and images still match the oracle, and the per-Gaussian lambda and
+    the cached slice state take the same path."""
+    scene = synth.with_learnable_lambda(synth.scene_cube(4099, 77), 3)
+    cams = [synth.look_at_camera((4.0, 0.5, 0.2), 96, 72), synth.look_at_camera((-1.0, 3.8, 0.5), 64, 80)]
+    st = _settings(None)
+    r, params, img = _render(scene, cams)
+    assert int(r.status.item()) == 0
+    views = r.split(img)
+    for v in range(2):
+        prep, member = _check_records(r, scene, cams, st, v)
+        _check_tiles(r, scene, cams, st, v, _all_tiles(cams[v], st), prep, member, views[v].cpu().numpy())
+    params["cond_cache"] = sx.condition_cache(params)
+    img_c = r.forward(params)
+    torch.cuda.synchronize()
+    assert torch.equal(img_c, img)
