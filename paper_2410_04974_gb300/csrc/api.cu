@@ -33,6 +33,9 @@ enum {
 };
 
 constexpr int kMaxCams = 256;
+// WS_COUNTERS words: 0 compaction, 1-4 depth passes, 8 emission, 9-12 tile
+// passes, 32 persistent blend queue, 40-44 depth-pass buffer parities
+constexpr int kDepthParityWord = 40;
 constexpr int kCamsPerUpload = 48;   // 6 KB of kernel parameters per upload
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -317,15 +320,18 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 8));
     launch_compact(a, grid, stream);
   }
-  // 2. depth passes (A -> B -> A ...)
+  // 2. depth passes between buffers A and B; each pass records in a parity
+  // word where its output is, so that a pass whose digit is the same for
+  // every key (the high byte of depths within a factor of two) moves nothing
+  uint32_t* depth_parity = counters + kDepthParityWord;   // zeroed above: input in A
   const int depth_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->n_pairs + kSortTile - 1) / kSortTile, (int64_t)sms * 4));
   for (int pass = 0; pass < p->depth_passes; ++pass) {
     OnesweepArgs a;
-    const bool even = (pass % 2) == 0;
-    a.keys_in = ws_ptr<uint32_t>(ws, p, even ? WS_DEPTH_A_K : WS_DEPTH_B_K);
-    a.vals_in = ws_ptr<uint32_t>(ws, p, even ? WS_DEPTH_A_V : WS_DEPTH_B_V);
-    a.keys_out = ws_ptr<uint32_t>(ws, p, even ? WS_DEPTH_B_K : WS_DEPTH_A_K);
-    a.vals_out = ws_ptr<uint32_t>(ws, p, even ? WS_DEPTH_B_V : WS_DEPTH_A_V);
+    a.keys[0] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_A_K);
+    a.vals[0] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_A_V);
+    a.keys[1] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_B_K);
+    a.vals[1] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_B_V);
+    a.parity = depth_parity + pass;
     a.n_ptr = counts + 0;
     a.capacity = (uint32_t)p->n_pairs;
     a.hist = hist + pass * 256;
@@ -336,11 +342,12 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
     a.status = status_dev;
     launch_onesweep(a, depth_grid, stream);
   }
-  const bool depth_in_a = (p->depth_passes % 2) == 0;
   // 3. duplicate emission in depth order + tile histograms
   {
     EmitArgs a;
-    a.pairs = ws_ptr<uint32_t>(ws, p, depth_in_a ? WS_DEPTH_A_V : WS_DEPTH_B_V);
+    a.pairs[0] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_A_V);
+    a.pairs[1] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_B_V);
+    a.depth_parity = depth_parity + p->depth_passes;
     a.n_vis = counts + 0;
     a.ntiles = ws_ptr<uint32_t>(ws, p, SIXDGS_WS_NTILES);
     a.rect = ws_ptr<ushort4>(ws, p, SIXDGS_WS_RECT);
@@ -350,7 +357,8 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
     a.keys_out = ws_ptr<uint32_t>(ws, p, WS_DUP_A_K);
     a.vals_out = ws_ptr<uint32_t>(ws, p, WS_DUP_A_V);
     // the depth keys are not needed once the depth passes are done
-    a.dup_off = ws_ptr<uint32_t>(ws, p, depth_in_a ? WS_DEPTH_A_K : WS_DEPTH_B_K);
+    a.dup_off[0] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_A_K);
+    a.dup_off[1] = ws_ptr<uint32_t>(ws, p, WS_DEPTH_B_K);
     a.chunk_first = ws_ptr<uint32_t>(ws, p, WS_CHUNK_FIRST);
     a.capacity = (uint64_t)p->dup_capacity;
     a.k_out = counts + 1;
@@ -369,12 +377,14 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
   // 4. tile passes
   const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->dup_capacity + kSortTile - 1) / kSortTile, (int64_t)sms * 4));
   for (int pass = 0; pass < p->tile_passes; ++pass) {
+    // fixed ping-pong: the sorted duplicates end in the buffer the plan names
     OnesweepArgs a;
     const bool even = (pass % 2) == 0;
-    a.keys_in = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_A_K : WS_DUP_B_K);
-    a.vals_in = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_A_V : WS_DUP_B_V);
-    a.keys_out = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_B_K : WS_DUP_A_K);
-    a.vals_out = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_B_V : WS_DUP_A_V);
+    a.keys[0] = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_A_K : WS_DUP_B_K);
+    a.vals[0] = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_A_V : WS_DUP_B_V);
+    a.keys[1] = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_B_K : WS_DUP_A_K);
+    a.vals[1] = ws_ptr<uint32_t>(ws, p, even ? WS_DUP_B_V : WS_DUP_A_V);
+    a.parity = nullptr;
     a.n_ptr = counts + 1;
     a.capacity = (uint32_t)p->dup_capacity;
     a.hist = hist + (p->depth_passes + pass) * 256;

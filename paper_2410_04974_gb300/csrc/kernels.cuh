@@ -47,10 +47,12 @@ struct CompactArgs {
 };
 
 struct OnesweepArgs {
-  const uint32_t* keys_in;
-  const uint32_t* vals_in;
-  uint32_t* keys_out;
-  uint32_t* vals_out;
+  uint32_t* keys[2];       // the two key buffers; data moves from one to the other
+  uint32_t* vals[2];
+  // null: input in keys[0], output in keys[1]; else *parity is the input
+  // buffer and the pass writes its output buffer to parity[1] (an identity
+  // pass leaves the data where it is)
+  uint32_t* parity;
   const uint32_t* n_ptr;   // element count (device)
   uint32_t capacity;       // buffer size; counts above it are clamped
   const uint32_t* hist;    // 256 digit counts of this pass
@@ -64,7 +66,8 @@ struct OnesweepArgs {
 // Duplicate emission in depth order (scan of ntiles over the depth-sorted
 // visible pairs) feeding the tile sort.
 struct EmitArgs {
-  const uint32_t* pairs;      // depth-sorted visible pair indices
+  const uint32_t* pairs[2];   // depth-sorted visible pair indices: pairs[*depth_parity]
+  const uint32_t* depth_parity;
   const uint32_t* n_vis;
   const uint32_t* ntiles;
   const ushort4* rect;
@@ -73,7 +76,7 @@ struct EmitArgs {
   uint32_t n_pairs;
   uint32_t* keys_out;         // global tile id
   uint32_t* vals_out;         // pair index
-  uint32_t* dup_off;          // first output of each depth-sorted pair (n_vis)
+  uint32_t* dup_off[2];       // first output of each depth-sorted pair (n_vis): dup_off[*depth_parity]
   uint32_t* chunk_first;      // pair owning the first output of each chunk
   uint64_t capacity;
   uint32_t* k_out;            // number of duplicates (may exceed capacity)

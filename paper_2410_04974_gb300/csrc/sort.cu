@@ -152,15 +152,17 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(CompactArgs a) {
     uint64_t off = s_excl + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      if (cnt[k] > 0u) {
-        uint32_t key = a.depth_key[base + k];
+      const bool vis = cnt[k] > 0u;
+      const uint32_t key = vis ? a.depth_key[base + k] : 0u;
+      if (vis) {
         if (off < n) {
           a.keys_out[off] = key;
           a.vals_out[off] = (uint32_t)(base + k);
         }
         ++off;
-        for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
       }
+      if (vis)
+        for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
     }
     if (tile == num_tiles - 1 && threadIdx.x == 0) *a.n_vis_out = (uint32_t)(s_excl + total);
   }
@@ -185,6 +187,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
   __shared__ uint32_t s_warp[WARPS + 1];
   __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // input buffer: fixed (parity == null) or as the previous pass left it
+  const uint32_t par = a.parity ? *a.parity : 0u;
+  // (selects, not an index: a runtime index into the parameter arrays would
+  // copy them to local memory)
+  const uint32_t* keys_in = par ? a.keys[1] : a.keys[0];
+  const uint32_t* vals_in = par ? a.vals[1] : a.vals[0];
+  uint32_t* keys_out = par ? a.keys[0] : a.keys[1];
+  uint32_t* vals_out = par ? a.vals[0] : a.vals[1];
   const uint32_t n = min(*a.n_ptr, a.capacity);
   const uint32_t num_tiles = (n + kSortTile - 1) / kSortTile;
   // exclusive digit offsets of the whole pass (thread tid owns digit tid)
@@ -192,15 +202,21 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
   const uint32_t my_count = a.hist[tid];
   const uint32_t hist_excl = block_excl_scan<kSortThreads>(my_count, htot, s_warp);
   const uint32_t lt_mask = (1u << lane) - 1u;
-  // Every key has the same digit: the stable pass is the identity, so the
-  // tiles are copied through without ranking or look-back.
+  // Every key has the same digit: the stable pass is the identity.  With a
+  // parity word the data stays where it is (the next reader is told so);
+  // otherwise the tiles are copied through without ranking or look-back.
   if (__syncthreads_or(n > 0u && my_count == n)) {
+    if (a.parity) {
+      if (blockIdx.x == 0 && tid == 0) a.parity[1] = par;
+      return;
+    }
     for (uint32_t i = blockIdx.x * kSortThreads + tid; i < n; i += gridDim.x * kSortThreads) {
-      a.keys_out[i] = a.keys_in[i];
-      a.vals_out[i] = a.vals_in[i];
+      keys_out[i] = keys_in[i];
+      vals_out[i] = vals_in[i];
     }
     return;
   }
+  if (a.parity && blockIdx.x == 0 && tid == 0) a.parity[1] = par ^ 1u;
   while (true) {
     __syncthreads();
     if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
@@ -216,8 +232,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
     for (int j = 0; j < kSortItems; ++j) {
       uint32_t idx = wbase + j * 32 + lane;
       bool valid = idx < n;
-      key[j] = valid ? a.keys_in[idx] : 0xffffffffu;
-      val[j] = valid ? a.vals_in[idx] : 0u;
+      key[j] = valid ? keys_in[idx] : 0xffffffffu;
+      val[j] = valid ? vals_in[idx] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
@@ -287,8 +303,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
       uint32_t k = s_keys[i];
       uint32_t out = s_glob[(k >> a.shift) & 255u] + i;
       if (out < n) {
-        a.keys_out[out] = k;
-        a.vals_out[out] = s_vals[i];
+        keys_out[out] = k;
+        vals_out[out] = s_vals[i];
       }
     }
   }
@@ -306,9 +322,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
 //   emit_expand_kernel -- one chunk per CTA at a time: the chunk's pairs
 //                         (at most kEmitChunk + 1, since every visible pair
 //                         has at least one tile) are staged in shared
-//                         memory, then consecutive threads write consecutive
-//                         duplicates, each finding its pair by binary search
-//                         over the staged offsets, so stores are coalesced.
+//                         memory, each marks the chunk position where its
+//                         outputs start, a prefix maximum over the positions
+//                         gives every output its pair, and consecutive
+//                         threads write consecutive duplicates, so stores are
+//                         coalesced.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(EmitArgs a) {
   __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
@@ -317,6 +335,9 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(EmitArgs a) {
   const uint32_t n_vis = *a.n_vis;
   const uint32_t num_tiles = (n_vis + kScanTile - 1) / kScanTile;
   const unsigned long long cap = a.capacity;
+  const uint32_t par = *a.depth_parity;
+  const uint32_t* pairs = par ? a.pairs[1] : a.pairs[0];
+  uint32_t* dup_off = par ? a.dup_off[1] : a.dup_off[0];
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
@@ -329,7 +350,7 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(EmitArgs a) {
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       bool valid = base + k < n_vis;
-      const uint32_t p = valid ? a.pairs[base + k] : 0u;
+      const uint32_t p = valid ? pairs[base + k] : 0u;
       valid = valid && p < a.n_pairs;
       cnt[k] = valid ? a.ntiles[p] : 0u;
       sum += cnt[k];
@@ -345,7 +366,7 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(EmitArgs a) {
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       if (base + k < n_vis) {
-        a.dup_off[base + k] = (uint32_t)min(off, 0xffffffffull);
+        dup_off[base + k] = (uint32_t)min(off, 0xffffffffull);
         // chunk boundaries b in [off, off + cnt) below the capacity
         const unsigned long long end = min(off + cnt[k], cap);
         for (unsigned long long b = (off + kEmitChunk - 1) / kEmitChunk * kEmitChunk; b < end; b += kEmitChunk)
@@ -377,12 +398,18 @@ __global__ void __launch_bounds__(kScanThreads) emit_expand_kernel(EmitArgs a) {
   __shared__ uint32_t s_pair[kMaxPairs];
   __shared__ uint32_t s_base[kMaxPairs];       // key of the pair's top-left tile
   __shared__ uint32_t s_shape[kMaxPairs];      // rect width | tiles_x << 16
+  __shared__ uint32_t s_owner[kEmitChunk];     // staged pair of every output of the chunk
+  __shared__ uint32_t s_wmax[kScanThreads / 32];
   __shared__ uint32_t s_hist[4 * 256];
+  static_assert(kEmitChunk == 2 * kScanThreads, "two outputs per thread in the owner scan");
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n_vis = *a.n_vis;
   const uint32_t k_all = (uint32_t)min((unsigned long long)*a.k_out, (unsigned long long)a.capacity);
   const uint32_t n_chunks = n_vis ? (k_all + kEmitChunk - 1) / kEmitChunk : 0u;
+  const uint32_t par = *a.depth_parity;
+  const uint32_t* pairs = par ? a.pairs[1] : a.pairs[0];
+  const uint32_t* dup_off = par ? a.dup_off[1] : a.dup_off[0];
   for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
     const uint32_t o0 = c * kEmitChunk;
     const uint32_t o1 = min(k_all, o0 + kEmitChunk);
@@ -395,11 +422,18 @@ __global__ void __launch_bounds__(kScanThreads) emit_expand_kernel(EmitArgs a) {
     e1 = max(min(e1, n_vis - 1), e0);
     const int m = (int)min(e1 - e0 + 1u, (uint32_t)kMaxPairs);
     __syncthreads();
+    for (int i = threadIdx.x; i < kEmitChunk; i += kScanThreads) s_owner[i] = 0u;
+    __syncthreads();
     for (int i = threadIdx.x; i < m; i += kScanThreads) {
       const uint32_t e = e0 + i;
-      const uint32_t p = a.pairs[e];
-      s_start[i] = a.dup_off[e];
+      const uint32_t p = pairs[e];
+      const uint32_t st = dup_off[e];
+      s_start[i] = st;
       s_pair[i] = p;
+      // a pair's outputs start at most once in the chunk (every visible pair
+      // has at least one), so each position is marked by at most one pair
+      const int64_t lp = (int64_t)st - (int64_t)o0;
+      if (lp >= 0 && lp < kEmitChunk) s_owner[lp] = (uint32_t)i;
       uint32_t base = 0, shape = 1;
       if (p < a.n_pairs) {
         const CamRec& cam = a.cams[p / (uint32_t)a.n];
@@ -411,20 +445,33 @@ __global__ void __launch_bounds__(kScanThreads) emit_expand_kernel(EmitArgs a) {
       s_shape[i] = shape;
     }
     __syncthreads();
-    int lo_prev = 0;
+    // The owner of output o is the last staged pair whose outputs start at
+    // or before o: an inclusive prefix maximum of the marks (unmarked
+    // positions hold 0, the chunk's first pair).  Thread t scans positions
+    // 2t and 2t + 1.
+    {
+      const uint32_t m0 = s_owner[2 * threadIdx.x];
+      const uint32_t m1 = max(m0, s_owner[2 * threadIdx.x + 1]);
+      uint32_t x = m1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = max(x, y);
+      }
+      if (lane == 31) s_wmax[warp] = x;
+      uint32_t before = __shfl_up_sync(0xffffffffu, x, 1);
+      if (lane == 0) before = 0u;
+      __syncthreads();
+      for (int w = 0; w < warp; ++w) before = max(before, s_wmax[w]);
+      s_owner[2 * threadIdx.x] = max(before, m0);
+      s_owner[2 * threadIdx.x + 1] = max(before, m1);
+    }
+    __syncthreads();
     for (uint32_t o1r = o0; o1r < o1; o1r += kScanThreads) {
       const uint32_t o = o1r + threadIdx.x;
       uint32_t key = 0xffffffffu;
       if (o < o1) {
-        // last staged pair whose first output is <= o (outputs increase by
-        // kScanThreads per step, so the previous answer bounds this one)
-        int lo = lo_prev, hi = m - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (s_start[mid] <= o) lo = mid;
-          else hi = mid - 1;
-        }
-        lo_prev = lo;
+        const int lo = (int)min(s_owner[o - o0], (uint32_t)(m - 1));
         const uint32_t local = o - s_start[lo];
         const uint32_t shape = s_shape[lo];
         const uint32_t w = shape & 0xffffu, tiles_x = shape >> 16;
