@@ -266,21 +266,36 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
       st_volatile(&lb[tid], kFlagInc | cnt);
     } else {
       st_volatile(&lb[tile * 256 + tid], kFlagAgg | cnt);
+      // Walk back over the predecessors' words for this digit, kWindow at a
+      // time (all loads in flight together), summing aggregates up to the
+      // first inclusive prefix; a word not yet published is waited for.
+      constexpr int kWindow = 8;
       long long p = (long long)tile - 1;
       const long long t0 = clock64();
       while (p >= 0) {
-        uint32_t w = ld_volatile(&lb[p * 256 + tid]);
-        uint32_t f = w & kFlagMask;
-        if (f == 0u) {
-          if (clock64() - t0 > a.spin_budget) {
-            raise_status(a.status, SIXDGS_ERR_TIMEOUT);
-            break;
+        uint32_t w[kWindow];
+#pragma unroll
+        for (int i = 0; i < kWindow; ++i) w[i] = (p - i >= 0) ? ld_volatile(&lb[(p - i) * 256 + tid]) : kFlagInc;
+        int used = 0;
+        bool found = false, waiting = false;
+#pragma unroll
+        for (int i = 0; i < kWindow; ++i) {
+          if (found || waiting) continue;
+          const uint32_t f = w[i] & kFlagMask;
+          if (f == 0u) {
+            waiting = true;
+            continue;
           }
-          continue;
+          excl += w[i] & kValMask;
+          ++used;
+          found = f == kFlagInc;
         }
-        excl += w & kValMask;
-        if (f == kFlagInc) break;
-        --p;
+        if (found) break;
+        p -= used;
+        if (waiting && clock64() - t0 > a.spin_budget) {
+          raise_status(a.status, SIXDGS_ERR_TIMEOUT);
+          break;
+        }
       }
       st_volatile(&lb[tile * 256 + tid], kFlagInc | ((excl + cnt) & kValMask));
     }
