@@ -493,7 +493,6 @@ sixdgs_status sixdgs_project_bwd(const sixdgs_plan* p, const sixdgs_scene* scene
                                  size_t ws_bytes, float* grad_mu_p, float* grad_mu_d, float* grad_l_raw,
                                  float* grad_opacity_logit, float* grad_sh, float* grad_lambda_raw,
                                  int32_t accumulate, int32_t* status_dev, sixdgs_stream_t stream_) {
-  (void)status_dev;
   sixdgs_status e = check_ws(p, ws, ws_bytes);
   if (e != SIXDGS_OK) return e;
   if (p->settings.inference) return SIXDGS_ERR_INVALID_ARG;
@@ -523,6 +522,9 @@ sixdgs_status sixdgs_project_bwd(const sixdgs_plan* p, const sixdgs_scene* scene
   b.grad_sh = grad_sh;
   b.grad_lambda_raw = grad_lambda_raw;
   b.accumulate = accumulate;
+  b.bulk = bulk_planes(p->n, {b.mu_p, b.mu_d, b.l_raw, b.opacity_logit, b.sh, b.lambda_raw});
+  b.spin_budget = spin_budget(p);
+  b.status = status_dev;
   launch_sh_bwd(b, stream);
   launch_geom_bwd(b, stream);
   return launch_status();

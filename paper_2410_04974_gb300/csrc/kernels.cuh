@@ -146,6 +146,9 @@ struct ProjectBwdArgs {
   float* grad_sh;
   float* grad_lambda_raw;
   int32_t accumulate;   // 1: add into the outputs instead of overwriting
+  int32_t bulk;         // 1: the parameter planes can be staged with bulk copies
+  int64_t spin_budget;
+  int32_t* status;
 };
 
 struct CondCacheArgs {

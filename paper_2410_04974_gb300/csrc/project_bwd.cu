@@ -45,22 +45,29 @@ __global__ void __launch_bounds__(128, 4) sh_bwd_kernel(ProjectBwdArgs a) {
     }
   float dmp[3] = {0.f, 0.f, 0.f};
   const float4* grec = reinterpret_cast<const float4*>(a.grad_rec);
-  // The next camera's tile count and colour gradients are loaded one
-  // iteration ahead (in bounds for every camera; ignored where the pair is
-  // not visible), so their latency overlaps this camera's arithmetic.
+  // Loads run ahead of the camera loop: the tile count two cameras ahead,
+  // and the next camera's colour gradients only where its pair is visible
+  // (its count arrived an iteration earlier), so their latency overlaps this
+  // camera's arithmetic and no invisible pair's record is read.
   uint32_t nt_next = a.ntiles[g];
-  float4 gb_next = grec[g * 3 + 1];
-  float gbz_next = grec[g * 3 + 2].x;
+  uint32_t nt_next2 = a.n_cams > 1 ? a.ntiles[n + g] : 0u;
+  float4 gb_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  float gbz_next = 0.f;
+  if (nt_next) {
+    gb_next = grec[g * 3 + 1];
+    gbz_next = grec[g * 3 + 2].x;
+  }
   for (int v = 0; v < a.n_cams; ++v) {
     const uint32_t nt = nt_next;
     const float4 gb = gb_next;
     const float gbz = gbz_next;
-    if (v + 1 < a.n_cams) {
+    nt_next = nt_next2;
+    if (nt_next) {
       const int64_t next = (int64_t)(v + 1) * n + g;
-      nt_next = a.ntiles[next];
       gb_next = grec[next * 3 + 1];
       gbz_next = grec[next * 3 + 2].x;
     }
+    nt_next2 = v + 2 < a.n_cams ? a.ntiles[(int64_t)(v + 2) * n + g] : 0u;
     if (nt == 0u) continue;
     const float drgb[3] = {gb.z, gb.w, gbz};
     if (drgb[0] == 0.f && drgb[1] == 0.f && drgb[2] == 0.f) continue;
@@ -144,18 +151,25 @@ __global__ void __launch_bounds__(128, 4) geom_bwd_kernel(ProjectBwdArgs a) {
   float gmp[3] = {0.f, 0.f, 0.f}, gmd[3] = {0.f, 0.f, 0.f}, galpha = 0.f, glam = 0.f;
   const float4* grec = reinterpret_cast<const float4*>(a.grad_rec);
 
-  // next camera's count and record gradients loaded one iteration ahead
+  // the count two cameras ahead and the next camera's record gradients
+  // (only where that pair is visible) loaded ahead of the camera loop
   uint32_t nt_next = a.ntiles[g];
-  float4 ga_next = grec[g * 3], gb_next = grec[g * 3 + 1];
+  uint32_t nt_next2 = a.n_cams > 1 ? a.ntiles[n + g] : 0u;
+  float4 ga_next = make_float4(0.f, 0.f, 0.f, 0.f), gb_next = ga_next;
+  if (nt_next) {
+    ga_next = grec[g * 3];
+    gb_next = grec[g * 3 + 1];
+  }
   for (int v = 0; v < a.n_cams && ok; ++v) {
     const uint32_t nt = nt_next;
     const float4 ga = ga_next, gb = gb_next;
-    if (v + 1 < a.n_cams) {
+    nt_next = nt_next2;
+    if (nt_next) {
       const int64_t next = (int64_t)(v + 1) * n + g;
-      nt_next = a.ntiles[next];
       ga_next = grec[next * 3];
       gb_next = grec[next * 3 + 1];
     }
+    nt_next2 = v + 2 < a.n_cams ? a.ntiles[(int64_t)(v + 2) * n + g] : 0u;
     if (nt == 0u) continue;
     const CamRec& cam = s_cams[v];
     // ---- forward recomputation (same arithmetic as project_fwd_kernel) ----
