@@ -109,6 +109,38 @@ __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, i
   }
 }
 
+// The backward walk runs in two passes per warp so that no value has to be
+// summed across the lanes of a warp for every list entry:
+//  1. pixel-parallel (lane = pixel), front to back like the forward: the
+//     transmittance T and the running dL/dC . (colour prefix) Q are carried
+//     per pixel, and each pixel's dL/dq and blend weight w for the entry are
+//     written to the warp's shared-memory slots (kSlots = 8 entries at a
+//     time);
+//  2. entry-parallel, once the slots are full (or the batch ends): lane
+//     8 r + s takes slot s over row r of the 8 x 4 sub-block and sums, over
+//     the row's 8 pixels, dq, c dq, c^2 dq and dL/dC . w (c the column
+//     relative to the sub-block's centre); the four rows are added with
+//     shuffles, and lane s turns the sums into the entry's nine record
+//     gradients (moments of dq in dx = u - px, dy = v - py) and adds them to
+//     the record gradients in global memory.
+// Pass 2 reads what pass 1 stored for a slot at pixel p from index p ^ s, so
+// the row writes of pass 1 and the column reads of pass 2 are both free of
+// shared-memory bank conflicts.
+constexpr int kSlots = 8;
+constexpr int kCullGroups = 64;   // 2,048 list entries
+struct __align__(16) WarpScratch {
+  float2 dqw[kSlots][32];   // (dL/dq / ln 2, w) of slot s at pixel p, at [s][p ^ s]
+  float4 pix[35];           // dL/dC of pixel p at p + (p >> 3) (rows in other banks)
+  int slot_j[kSlots];       // batch index of the entry in slot s
+  // fused kernel: the forward walk's culling ballot of list entries
+  // [32 g, 32 g + 32) of the tile's list (first kCullGroups groups)
+  uint32_t cull[kCullGroups];
+};
+
+__host__ __device__ constexpr int bwd_scratch_bytes(int threads) {
+  return (threads / 32) * (int)sizeof(WarpScratch);
+}
+
 // Per-pixel front-to-back walk of a tile's list (the forward blend): T and
 // C accumulate over the entries that reach the warp's sub-block; walked is
 // the number of list entries before the stop (the list length if none).
@@ -118,10 +150,13 @@ struct FwdPixel {
   bool staged;   // the whole list was loaded as one batch (CTA-uniform)
 };
 
+// cull (fused kernel, else null): the exact sub-block test is used and each
+// group's ballot is recorded there for the backward walk.
 template <bool kCount>
 __device__ __forceinline__ FwdPixel fwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
                                              uint2 range, bool inside, float4* s_a, float4* s_b, float4* s_c,
-                                             uint32_t& n_eval, uint32_t& n_comp, uint32_t& n_warp) {
+                                             uint32_t& n_eval, uint32_t& n_comp, uint32_t& n_warp,
+                                             uint32_t* cull = nullptr) {
   const int B = a.batch;
   const int lane = threadIdx.x & 31;
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
@@ -137,8 +172,13 @@ __device__ __forceinline__ FwdPixel fwd_walk(const BlendArgs& a, const PixelMap&
     if (__all_sync(0xffffffffu, done)) continue;
     for (int base = 0; base < cnt; base += 32) {
       const int jl = base + lane;
-      const bool rel = jl < cnt && reaches<false>(pm, s_a[jl], s_b[jl], s_c[jl]);
+      const bool rel = jl < cnt && (cull ? reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl])
+                                         : reaches<false>(pm, s_a[jl], s_b[jl], s_c[jl]));
       uint32_t mask = __ballot_sync(0xffffffffu, rel);
+      if (cull) {
+        const uint32_t g = (start - range.x + base) >> 5;
+        if (lane == 0 && g < kCullGroups) cull[g] = mask;
+      }
       if (kCount) n_warp += __popc(mask);
       while (mask) {
         const int j = base + __ffs(mask) - 1;
@@ -244,34 +284,6 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
 }
 
-// The backward walk runs in two passes per warp so that no value has to be
-// summed across the lanes of a warp for every list entry:
-//  1. pixel-parallel (lane = pixel), front to back like the forward: the
-//     transmittance T and the running dL/dC . (colour prefix) Q are carried
-//     per pixel, and each pixel's dL/dq and blend weight w for the entry are
-//     written to the warp's shared-memory slots (kSlots = 8 entries at a
-//     time);
-//  2. entry-parallel, once the slots are full (or the batch ends): lane
-//     8 r + s takes slot s over row r of the 8 x 4 sub-block and sums, over
-//     the row's 8 pixels, dq, c dq, c^2 dq and dL/dC . w (c the column
-//     relative to the sub-block's centre); the four rows are added with
-//     shuffles, and lane s turns the sums into the entry's nine record
-//     gradients (moments of dq in dx = u - px, dy = v - py) and adds them to
-//     the record gradients in global memory.
-// Pass 2 reads what pass 1 stored for a slot at pixel p from index p ^ s, so
-// the row writes of pass 1 and the column reads of pass 2 are both free of
-// shared-memory bank conflicts.
-constexpr int kSlots = 8;
-struct __align__(16) WarpScratch {
-  float2 dqw[kSlots][32];   // (dL/dq / ln 2, w) of slot s at pixel p, at [s][p ^ s]
-  float4 pix[35];           // dL/dC of pixel p at p + (p >> 3) (rows in other banks)
-  int slot_j[kSlots];       // batch index of the entry in slot s
-};
-
-__host__ __device__ constexpr int bwd_scratch_bytes(int threads) {
-  return (threads / 32) * (int)sizeof(WarpScratch);
-}
-
 // Pass 2 over slots [0, k).  xc, yc: centre of the 8 x 4 sub-block.
 __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws, int k, const float4* s_a,
                                             const float4* s_c, float xc, float yc) {
@@ -332,7 +344,7 @@ template <bool kRecompute>
 __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
                                          uint2 range, bool inside, const float* Cf, const float* dC,
                                          uint32_t bound, bool staged, float4* s_a, float4* s_b, float4* s_c,
-                                         WarpScratch& ws) {
+                                         WarpScratch& ws, bool recorded = false) {
   const int B = a.batch;
   const int lane = threadIdx.x & 31;
   // dL/dalpha_i = sum_c dC_c (c_i T_i - S_c / (1 - alpha_i)) with S the colour
@@ -354,9 +366,17 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
     // entries j < lim of this batch lie within the pixel's walk
     const int lim = (int)min((uint32_t)cnt, bound - min(bound, start - range.x));
     for (int base = 0; base < cnt; base += 32) {
-      const int jl = base + lane;
-      const bool rel = jl < cnt && reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl]);
-      uint32_t mask = __ballot_sync(0xffffffffu, rel);
+      // the sub-block test of these 32 entries: recorded by the fused
+      // kernel's forward walk (the list is the same), else evaluated here
+      const uint32_t g = (start - range.x + base) >> 5;
+      uint32_t mask;
+      if (recorded && g < kCullGroups) {
+        mask = ws.cull[g];
+      } else {
+        const int jl = base + lane;
+        const bool rel = jl < cnt && reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl]);
+        mask = __ballot_sync(0xffffffffu, rel);
+      }
       while (mask) {
         const int j = base + __ffs(mask) - 1;
         mask &= mask - 1;
@@ -458,8 +478,10 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
   const uint2 range = a.ranges[gt];
   const int lane = threadIdx.x & 31;
 
+  WarpScratch& ws = reinterpret_cast<WarpScratch*>(s_mem + 3 * B)[threadIdx.x >> 5];
   uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
-  const FwdPixel fp = fwd_walk<false>(a, pm, pxc, pyc, range, inside, s_a, s_b, s_c, n_eval, n_comp, n_warp);
+  const FwdPixel fp =
+      fwd_walk<false>(a, pm, pxc, pyc, range, inside, s_a, s_b, s_c, n_eval, n_comp, n_warp, ws.cull);
   float Cf[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f};
   float l1 = 0.f;
   if (inside) {
@@ -492,9 +514,8 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += s_red[w];
     atomicAdd(a.loss, sum * (double)a.inv_count);
   }
-  WarpScratch* ws = reinterpret_cast<WarpScratch*>(s_mem + 3 * B);
-  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_a, s_b, s_c,
-                  ws[threadIdx.x >> 5]);
+  __syncwarp();
+  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_a, s_b, s_c, ws, true);
 }
 
 // Register budgets of the kernels that run the backward walk (swept on the
