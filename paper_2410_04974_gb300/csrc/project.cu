@@ -100,6 +100,16 @@ __device__ __forceinline__ SliceView slice_view(const float* mp, const float* md
   return s;
 }
 
+// The matrix with its lower triangle replaced by the upper one (the state
+// the projection works with is symmetric by construction).
+__device__ __forceinline__ M3 sym_upper(const M3& m) {
+  M3 r = m;
+  r(1, 0) = m(0, 1);
+  r(2, 0) = m(0, 2);
+  r(2, 1) = m(1, 2);
+  return r;
+}
+
 // Per-Gaussian state the second phase reads from shared memory, written over
 // the tile's conditioning planes once a thread has read its own: A (9), the
 // upper triangles of Sigma_d^-1 and Sigma_cond (6 each: 00 01 02 11 12 22),
@@ -126,6 +136,101 @@ __device__ __forceinline__ M3 load_sym(const float* cp, int k0) {
   return m;
 }
 
+// EWA projection, colour and tile rectangle of one pair that passed the
+// visibility test (section 4.4, section 4.2): writes the pair's record, depth
+// key, rect and tile count (0 when the 2D covariance, the footprint or a
+// value is degenerate).  beta(k, c): SH coefficient k of colour channel c.
+template <typename Beta>
+__device__ __forceinline__ void project_pair(const ProjectArgs& a, Beta beta, const float* mp,
+                                             const float* md, const M3& A, const M3& Sdi, const M3& Sc, float alpha,
+                                             float lam, const CamRec& cam, int64_t pair, int K) {
+  const SliceView sv = slice_view(mp, md, A, Sdi, alpha, lam, cam);
+  const float* t = sv.t;
+  const float alpha_cond = sv.alpha_cond;
+  uint32_t ntiles = 0;
+  // ---- projection (section 4.4, EWA) ----
+  float iz = 1.f / t[2];
+  float rx = fminf(cam.limx, fmaxf(-cam.limx, t[0] * iz));
+  float ry = fminf(cam.limy, fmaxf(-cam.limy, t[1] * iz));
+  float j00 = cam.fx * iz, j02 = -cam.fx * rx * iz;
+  float j11 = cam.fy * iz, j12 = -cam.fy * ry * iz;
+  // T = J R (2x3)
+  float T0[3], T1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    T0[j] = j00 * cam.r[j] + j02 * cam.r[6 + j];
+    T1[j] = j11 * cam.r[3 + j] + j12 * cam.r[6 + j];
+  }
+  float U0[3], U1[3];
+  mat_t_vec(Sc, T0, U0);  // Sigma_cond symmetric: (T0 Sc)_j
+  mat_t_vec(Sc, T1, U1);
+  float ca = U0[0] * T0[0] + U0[1] * T0[1] + U0[2] * T0[2] + kDilation;
+  float cb = U0[0] * T1[0] + U0[1] * T1[1] + U0[2] * T1[2];
+  float cc = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2] + kDilation;
+  float det = ca * cc - cb * cb;
+  if (det > 0.f) {
+    float idet = 1.f / det;
+    float con_a = cc * idet, con_b = -cb * idet, con_c = ca * idet;
+    float mid = 0.5f * (ca + cc);
+    float lmax = mid + sqrtf(fmaxf(mid * mid - det, 0.f));
+    float radius = kRadiusSigmas * sqrtf(lmax);
+    float u = cam.fx * t[0] * iz + cam.cx;
+    float w = cam.fy * t[1] * iz + cam.cy;
+    // Bounding box of the alpha >= 1/255 ellipse {Delta^T conic Delta <=
+    // 2 ln(255 alpha_cond)}: half-extents sqrt(L2 * Sigma_2D,ii), widened
+    // by a margin far above FP32 rounding, so that culling with it (the
+    // tile rectangle here, the blend's per-warp test) never drops an
+    // entry that a pixel composites.
+    const float lo = log2f(alpha_cond);
+    const float L2 = 2.f * kLn2 * fmaxf(lo - kQMin, 0.f);
+    const float hx = sqrtf(L2 * ca) * 1.0001f + 0.01f;
+    const float hy = sqrtf(L2 * cc) * 1.0001f + 0.01f;
+    const float ex = a.alpha_footprint ? fminf(radius, hx) : radius;
+    const float ey = a.alpha_footprint ? fminf(radius, hy) : radius;
+    float x0 = floorf((u - ex) * a.inv_tile_w), x1 = floorf((u + ex) * a.inv_tile_w) + 1.f;
+    float y0 = floorf((w - ey) * a.inv_tile_h), y1 = floorf((w + ey) * a.inv_tile_h) + 1.f;
+    x0 = fminf(fmaxf(x0, 0.f), (float)cam.tiles_x);
+    x1 = fminf(fmaxf(x1, 0.f), (float)cam.tiles_x);
+    y0 = fminf(fmaxf(y0, 0.f), (float)cam.tiles_y);
+    y1 = fminf(fmaxf(y1, 0.f), (float)cam.tiles_y);
+    bool finite = isfinite(u) && isfinite(w) && isfinite(radius) && isfinite(con_a) && isfinite(con_b) &&
+                  isfinite(con_c);
+    if (!finite) raise_status(a.status, SIXDGS_ERR_NONFINITE);
+    // ---- colour (section 4.2) ----
+    float Y[kMaxShCoeffs];
+    sh_basis(a.sh_degree, sv.d[0], sv.d[1], sv.d[2], Y);
+    float rgb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxShCoeffs; ++k)
+        if (k < K) s += beta(k, c) * Y[k];
+      rgb[c] = sigmoidf_(s);
+    }
+    if (finite && !(isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]))) {
+      finite = false;
+      raise_status(a.status, SIXDGS_ERR_NONFINITE);
+    }
+    if (finite && x0 < x1 && y0 < y1) {
+      ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
+      PairRec rec;
+      rec.a = make_float4(u, w, -0.5f * kLog2e * con_a, -kLog2e * con_b);
+      rec.b = make_float4(-0.5f * kLog2e * con_c, lo, rgb[0], rgb[1]);
+      rec.c = make_float4(rgb[2], hx, hy, t[2]);
+      a.rec[pair] = rec;
+      if (a.grad_rec) {
+        float4* gr = reinterpret_cast<float4*>(a.grad_rec) + pair * 3;
+        gr[0] = gr[1] = gr[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      a.depth_key[pair] = __float_as_uint(t[2]);
+      a.rect[pair] =
+          make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
+    }
+  }
+  a.ntiles[pair] = ntiles;
+}
+
 // kStageTile Gaussians per CTA in two phases:
 //  A. one thread per Gaussian: the tile's parameter planes are staged in
 //     shared memory (stage.cuh), the view-independent state is computed (or
@@ -135,8 +240,13 @@ __device__ __forceinline__ M3 load_sym(const float* cp, int k0) {
 //  B. the CTA's threads take the queued pairs densely, one pair each, for
 //     the EWA projection, colour and tile rectangle, so that the expensive
 //     part runs on full warps however many pairs a Gaussian has visible.
-template <bool kCached>
-__global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs a) {
+// kStaged (frames of several cameras, where each Gaussian's parameters serve
+// several pairs): as above.  Otherwise (one camera: little work to overlap
+// with an up-front load, at most one pair per Gaussian) each thread reads its
+// Gaussian's planes from global memory where it uses them and projects its
+// visible pair itself, with the same arithmetic.
+template <bool kCached, bool kStaged>
+__global__ void __launch_bounds__(kStageTile, kStaged ? 5 : 4) project_fwd_kernel(ProjectArgs a) {
   extern __shared__ float4 s_dyn[];
   __shared__ uint64_t s_bars[2];
   __shared__ uint32_t s_count;
@@ -144,8 +254,10 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
   float* tile = reinterpret_cast<float*>(s_cams + a.n_cams);
   const int64_t n = a.n;
   const ProjPlanes pp = proj_planes(kCached, a.sh_degree, a.lambda_raw != nullptr);
-  float* s_cs = tile + pp.cond * kStageTile;   // over the conditioning planes (phase A)
-  uint16_t* s_queue = reinterpret_cast<uint16_t*>(tile + pp.count * kStageTile);   // local | view << 7
+  // per-Gaussian state over the staged conditioning planes (read by phase A
+  // first); queue after the tile (staged path only)
+  float* s_cs = tile + pp.cond * kStageTile;
+  uint16_t* s_queue = reinterpret_cast<uint16_t*>(tile + pp.count * kStageTile);
   for (int i = threadIdx.x; i < a.n_cams; i += blockDim.x) s_cams[i] = a.cams[i];
   if (threadIdx.x == 0) s_count = 0;
   const int64_t g0 = (int64_t)blockIdx.x * kStageTile;
@@ -153,20 +265,34 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
   // group 0: mu_p, mu_d, the conditioning planes and lambda (phase A);
   // group 1: the SH coefficients, in flight while phase A runs
   const bool bulk = a.bulk != 0;
-  stage_issue(tile, pp.count, pp.sh, [&](int q) { return proj_src(a, pp, q); }, g0, m, bulk, s_bars);
-  if (!stage_wait(s_bars, 0, bulk, a.spin_budget)) raise_status(a.status, SIXDGS_ERR_TIMEOUT);
+  if (kStaged) {
+    stage_issue(tile, pp.count, pp.sh, [&](int q) { return proj_src(a, pp, q); }, g0, m, bulk, s_bars);
+    if (!stage_wait(s_bars, 0, bulk, a.spin_budget)) raise_status(a.status, SIXDGS_ERR_TIMEOUT);
+  } else {
+    __syncthreads();
+  }
   const int tid = threadIdx.x;
 
   // ---- phase A: per Gaussian ----
   if (tid < m) {
     const int64_t g = g0 + tid;
     const float* sp = tile + tid;
-    auto P = [&](int q) { return sp[q * kStageTile]; };
+    auto P = [&](int q) { return kStaged ? sp[q * kStageTile] : __ldg(proj_src(a, pp, q) + g); };
     float mp[3], md[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       mp[i] = P(pp.mu_p + i);
       md[i] = P(pp.mu_d + i);
+    }
+    // one camera: the SH coefficients are loaded with everything else, into
+    // registers (unused in the staged path, which reads shared memory)
+    float bt[kMaxShCoeffs][3];
+    if (!kStaged) {
+      const int Kb = (a.sh_degree + 1) * (a.sh_degree + 1);
+#pragma unroll
+      for (int k = 0; k < kMaxShCoeffs; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bt[k][c] = k < Kb ? __ldg(a.sh + (int64_t)(k * 3 + c) * n + g) : 0.f;
     }
     CondState cs;
     bool ok = true;
@@ -199,6 +325,24 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
            isfinite(md[1]) && isfinite(md[2]) && isfinite(cs.alpha) && isfinite(lam);
     }
     if (!ok) raise_status(a.status, SIXDGS_ERR_NONFINITE);
+    if (!kStaged) {
+      // one camera: project the pair right here (no queue, no second phase),
+      // with the same symmetric state the queued path reads
+      const M3 Sdi = sym_upper(cs.Sdi), Sc = sym_upper(cs.Sc);
+      const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+      for (int v = 0; v < a.n_cams; ++v) {
+        const int64_t pair = (int64_t)v * n + g;
+        bool vis = false;
+        if (ok) {
+          const SliceView sv = slice_view(mp, md, cs.A, Sdi, cs.alpha, lam, s_cams[v]);
+          vis = (sv.alpha_cond >= kAlphaMin) && (sv.t[2] > s_cams[v].znear);
+        }
+        if (vis) project_pair(a, [&](int k, int c) { return bt[k][c]; }, mp, md, cs.A, Sdi, Sc, cs.alpha, lam,
+                              s_cams[v], pair, K);
+        else a.ntiles[pair] = 0u;
+      }
+      return;
+    }
     // this thread's own column of the conditioning planes is read: reuse it
     float* cp = s_cs + tid;
 #pragma unroll
@@ -208,10 +352,11 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
     cp[21 * kStageTile] = cs.alpha;
     cp[22 * kStageTile] = lam;
     const int lane = tid & 31;
+    const M3 Sdi = sym_upper(cs.Sdi);   // as phase B reads it back
     for (int v = 0; v < a.n_cams; ++v) {
       bool vis = false;
       if (ok) {
-        const SliceView sv = slice_view(mp, md, cs.A, cs.Sdi, cs.alpha, lam, s_cams[v]);
+        const SliceView sv = slice_view(mp, md, cs.A, Sdi, cs.alpha, lam, s_cams[v]);
         vis = (sv.alpha_cond >= kAlphaMin) && (sv.t[2] > s_cams[v].znear);
       }
       if (!vis) a.ntiles[(int64_t)v * n + g] = 0u;
@@ -225,6 +370,7 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
       if (vis) s_queue[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(tid | (v << 7));
     }
   }
+  if (!kStaged) return;
   if (!stage_wait(s_bars, 1, bulk, a.spin_budget)) raise_status(a.status, SIXDGS_ERR_TIMEOUT);
   __syncthreads();
 
@@ -237,7 +383,7 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
     const int v = (int)(e >> 7);
     const int64_t pair = (int64_t)v * n + g0 + gl;
     const float* sp = tile + gl;
-    auto P = [&](int q) { return sp[q * kStageTile]; };
+    auto P = [&](int q) { return kStaged ? sp[q * kStageTile] : __ldg(proj_src(a, pp, q) + g0 + gl); };
     const float* cp = s_cs + gl;
     M3 A;
 #pragma unroll
@@ -246,106 +392,34 @@ __global__ void __launch_bounds__(kStageTile, 5) project_fwd_kernel(ProjectArgs 
     const float mp[3] = {P(pp.mu_p), P(pp.mu_p + 1), P(pp.mu_p + 2)};
     const float md[3] = {P(pp.mu_d), P(pp.mu_d + 1), P(pp.mu_d + 2)};
     const CamRec& cam = s_cams[v];
-    const SliceView sv = slice_view(mp, md, A, Sdi, cp[21 * kStageTile], cp[22 * kStageTile], cam);
-    const float* t = sv.t;
-    const float alpha_cond = sv.alpha_cond;
-    uint32_t ntiles = 0;
-    // ---- projection (section 4.4, EWA) ----
-    float iz = 1.f / t[2];
-    float rx = fminf(cam.limx, fmaxf(-cam.limx, t[0] * iz));
-    float ry = fminf(cam.limy, fmaxf(-cam.limy, t[1] * iz));
-    float j00 = cam.fx * iz, j02 = -cam.fx * rx * iz;
-    float j11 = cam.fy * iz, j12 = -cam.fy * ry * iz;
-    // T = J R (2x3)
-    float T0[3], T1[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T0[j] = j00 * cam.r[j] + j02 * cam.r[6 + j];
-      T1[j] = j11 * cam.r[3 + j] + j12 * cam.r[6 + j];
-    }
-    float U0[3], U1[3];
-    mat_t_vec(Sc, T0, U0);  // Sigma_cond symmetric: (T0 Sc)_j
-    mat_t_vec(Sc, T1, U1);
-    float ca = U0[0] * T0[0] + U0[1] * T0[1] + U0[2] * T0[2] + kDilation;
-    float cb = U0[0] * T1[0] + U0[1] * T1[1] + U0[2] * T1[2];
-    float cc = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2] + kDilation;
-    float det = ca * cc - cb * cb;
-    if (det > 0.f) {
-      float idet = 1.f / det;
-      float con_a = cc * idet, con_b = -cb * idet, con_c = ca * idet;
-      float mid = 0.5f * (ca + cc);
-      float lmax = mid + sqrtf(fmaxf(mid * mid - det, 0.f));
-      float radius = kRadiusSigmas * sqrtf(lmax);
-      float u = cam.fx * t[0] * iz + cam.cx;
-      float w = cam.fy * t[1] * iz + cam.cy;
-      // Bounding box of the alpha >= 1/255 ellipse {Delta^T conic Delta <=
-      // 2 ln(255 alpha_cond)}: half-extents sqrt(L2 * Sigma_2D,ii), widened
-      // by a margin far above FP32 rounding, so that culling with it (the
-      // tile rectangle here, the blend's per-warp test) never drops an
-      // entry that a pixel composites.
-      const float lo = log2f(alpha_cond);
-      const float L2 = 2.f * kLn2 * fmaxf(lo - kQMin, 0.f);
-      const float hx = sqrtf(L2 * ca) * 1.0001f + 0.01f;
-      const float hy = sqrtf(L2 * cc) * 1.0001f + 0.01f;
-      const float ex = a.alpha_footprint ? fminf(radius, hx) : radius;
-      const float ey = a.alpha_footprint ? fminf(radius, hy) : radius;
-      float x0 = floorf((u - ex) * a.inv_tile_w), x1 = floorf((u + ex) * a.inv_tile_w) + 1.f;
-      float y0 = floorf((w - ey) * a.inv_tile_h), y1 = floorf((w + ey) * a.inv_tile_h) + 1.f;
-      x0 = fminf(fmaxf(x0, 0.f), (float)cam.tiles_x);
-      x1 = fminf(fmaxf(x1, 0.f), (float)cam.tiles_x);
-      y0 = fminf(fmaxf(y0, 0.f), (float)cam.tiles_y);
-      y1 = fminf(fmaxf(y1, 0.f), (float)cam.tiles_y);
-      bool finite = isfinite(u) && isfinite(w) && isfinite(radius) && isfinite(con_a) && isfinite(con_b) &&
-                    isfinite(con_c);
-      if (!finite) raise_status(a.status, SIXDGS_ERR_NONFINITE);
-      // ---- colour (section 4.2) ----
-      float Y[kMaxShCoeffs];
-      sh_basis(a.sh_degree, sv.d[0], sv.d[1], sv.d[2], Y);
-      float rgb[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < kMaxShCoeffs; ++k)
-          if (k < K) s += P(pp.sh + k * 3 + c) * Y[k];
-        rgb[c] = sigmoidf_(s);
-      }
-      if (finite && !(isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]))) {
-        finite = false;
-        raise_status(a.status, SIXDGS_ERR_NONFINITE);
-      }
-      if (finite && x0 < x1 && y0 < y1) {
-        ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
-        PairRec rec;
-        rec.a = make_float4(u, w, -0.5f * kLog2e * con_a, -kLog2e * con_b);
-        rec.b = make_float4(-0.5f * kLog2e * con_c, lo, rgb[0], rgb[1]);
-        rec.c = make_float4(rgb[2], hx, hy, t[2]);
-        a.rec[pair] = rec;
-        if (a.grad_rec) {
-          float4* gr = reinterpret_cast<float4*>(a.grad_rec) + pair * 3;
-          gr[0] = gr[1] = gr[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        a.depth_key[pair] = __float_as_uint(t[2]);
-        a.rect[pair] =
-            make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
-      }
-    }
-    a.ntiles[pair] = ntiles;
+    project_pair(a, [&](int k, int c) { return P(pp.sh + k * 3 + c); }, mp, md, A, Sdi, Sc, cp[21 * kStageTile],
+                 cp[22 * kStageTile], cam, pair, K);
   }
+}
+
+template <bool kCached, bool kStaged>
+static void launch_project(const ProjectArgs& a, cudaStream_t stream) {
+  const int64_t blocks = (a.n + kStageTile - 1) / kStageTile;
+  const ProjPlanes pp = proj_planes(kCached, a.sh_degree, a.lambda_raw != nullptr);
+  const size_t smem = sizeof(CamRec) * (size_t)a.n_cams +
+                      (kStaged ? (size_t)pp.count * kStageTile * sizeof(float) +
+                                     (size_t)kStageTile * a.n_cams * sizeof(uint16_t)
+                               : 0);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(project_fwd_kernel<kCached, kStaged>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  project_fwd_kernel<kCached, kStaged><<<(unsigned)blocks, kStageTile, smem, stream>>>(a);
 }
 
 void launch_project_fwd(const ProjectArgs& a, cudaStream_t stream) {
   if (a.n == 0) return;
-  const int64_t blocks = (a.n + kStageTile - 1) / kStageTile;
-  const ProjPlanes pp = proj_planes(a.cond_cache != nullptr, a.sh_degree, a.lambda_raw != nullptr);
-  const size_t smem = sizeof(CamRec) * (size_t)a.n_cams + (size_t)pp.count * kStageTile * sizeof(float) +
-                      (size_t)kStageTile * a.n_cams * sizeof(uint16_t);
-  const void* fn = a.cond_cache ? (const void*)project_fwd_kernel<true> : (const void*)project_fwd_kernel<false>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (a.cond_cache)
-    project_fwd_kernel<true><<<(unsigned)blocks, kStageTile, smem, stream>>>(a);
-  else
-    project_fwd_kernel<false><<<(unsigned)blocks, kStageTile, smem, stream>>>(a);
+  const bool staged = a.n_cams > 1;
+  if (a.cond_cache) {
+    if (staged) launch_project<true, true>(a, stream);
+    else launch_project<true, false>(a, stream);
+  } else {
+    if (staged) launch_project<false, true>(a, stream);
+    else launch_project<false, false>(a, stream);
+  }
 }
 
 void launch_cond_cache(const CondCacheArgs& a, cudaStream_t stream) {

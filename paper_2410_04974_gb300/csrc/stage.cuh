@@ -71,8 +71,18 @@ template <typename Src>
 __device__ __forceinline__ void stage_issue(float* tile, int np, int split, Src src, int64_t g0, int m, bool bulk,
                                             uint64_t* bars) {
   if (!bulk) {
-    for (int q = 0; q < np; ++q)
-      if ((int)threadIdx.x < m) tile[q * kStageTile + threadIdx.x] = __ldg(src(q) + g0 + threadIdx.x);
+    // plain coalesced loads, kBurst planes in flight per thread
+    constexpr int kBurst = 16;
+    if ((int)threadIdx.x < m) {
+      for (int q0 = 0; q0 < np; q0 += kBurst) {
+        float v[kBurst];
+#pragma unroll
+        for (int i = 0; i < kBurst; ++i) v[i] = q0 + i < np ? __ldg(src(q0 + i) + g0 + threadIdx.x) : 0.f;
+#pragma unroll
+        for (int i = 0; i < kBurst; ++i)
+          if (q0 + i < np) tile[(q0 + i) * kStageTile + threadIdx.x] = v[i];
+      }
+    }
     __syncthreads();
     return;
   }
