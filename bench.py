@@ -71,9 +71,10 @@ SCALE_ROT_BYTES = (21 + 9 + 3) * 4
 # kernel's committed ncu summary (profiles/) only while these are unchanged.
 KERNEL_SOURCES = {
     "blend_fused_kernel": ["raster.cu"], "blend_bwd_kernel": ["raster.cu"], "blend_fwd_kernel": ["raster.cu"],
-    "project_fwd_kernel": ["project.cu", "cond.cuh", "sh.cuh", "mat3.cuh"],
-    "onesweep_kernel": ["sort.cu"], "emit_expand_kernel": ["sort.cu"],
+    "project_fwd_kernel": ["project.cu", "cond.cuh", "sh.cuh", "mat3.cuh", "stage.cuh"],
+    "onesweep_kernel": ["sort.cu"], "emit_expand_kernel": ["sort.cu"], "compact_kernel": ["sort.cu"],
     "geom_bwd_kernel": ["project_bwd.cu", "cond.cuh", "mat3.cuh"],
+    "sh_bwd_kernel": ["project_bwd.cu", "cond.cuh", "mat3.cuh", "sh.cuh"],
     "scale_rotation_kernel": ["scale_rotation.cu", "cond.cuh", "mat3.cuh"],
 }
 
