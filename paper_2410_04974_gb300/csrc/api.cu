@@ -316,7 +316,7 @@ sixdgs_status sixdgs_bin_sort(const sixdgs_plan* p, void* ws, size_t ws_bytes, i
     a.passes = p->depth_passes;
     a.spin_budget = budget;
     a.status = status_dev;
-    const int64_t tiles = (p->n_pairs + kScanTile - 1) / kScanTile;
+    const int64_t tiles = (p->n_pairs + kCompactTile - 1) / kCompactTile;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 8));
     launch_compact(a, grid, stream);
   }

@@ -186,6 +186,15 @@ void launch_geom_bwd(const ProjectBwdArgs& a, cudaStream_t stream);
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
+// the visible-pair compaction: more items per thread (loads in flight, fewer
+// look-back steps); a multiple of 4, so its tiles never outnumber the scan
+// tiles the workspace has state for
+#ifndef SIXDGS_COMPACT_ITEMS
+#define SIXDGS_COMPACT_ITEMS 16
+#endif
+constexpr int kCompactItems = SIXDGS_COMPACT_ITEMS;
+constexpr int kCompactTile = kScanThreads * kCompactItems;
+static_assert(kCompactItems % 4 == 0 && kCompactTile >= kScanTile, "compaction tile");
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 12;
 constexpr int kSortTile = kSortThreads * kSortItems;

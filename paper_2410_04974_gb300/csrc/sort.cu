@@ -123,25 +123,33 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(CompactArgs a) {
   __shared__ unsigned long long s_excl;
   for (int i = threadIdx.x; i < 4 * 256; i += kScanThreads) s_hist[i] = 0;
   const uint64_t n = (uint64_t)a.n_pairs;
-  const uint32_t num_tiles = (uint32_t)((n + kScanTile - 1) / kScanTile);
+  const uint32_t num_tiles = (uint32_t)((n + kCompactTile - 1) / kCompactTile);
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= num_tiles) break;
-    const uint64_t base = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
-    uint32_t cnt[kScanItems];
-    if (base + kScanItems <= n) {
-      uint4 q = *reinterpret_cast<const uint4*>(a.ntiles + base);
-      cnt[0] = q.x; cnt[1] = q.y; cnt[2] = q.z; cnt[3] = q.w;
+    const uint64_t base = (uint64_t)tile * kCompactTile + (uint64_t)threadIdx.x * kCompactItems;
+    uint32_t cnt[kCompactItems];
+    if (base + kCompactItems <= n) {
+#pragma unroll
+      for (int k = 0; k < kCompactItems; k += 4) {
+        const uint4 q = *reinterpret_cast<const uint4*>(a.ntiles + base + k);
+        cnt[k] = q.x; cnt[k + 1] = q.y; cnt[k + 2] = q.z; cnt[k + 3] = q.w;
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < kScanItems; ++k) cnt[k] = (base + k < n) ? a.ntiles[base + k] : 0u;
+      for (int k = 0; k < kCompactItems; ++k) cnt[k] = (base + k < n) ? a.ntiles[base + k] : 0u;
     }
+    // the depth keys of all items, loaded together (an invisible pair's key is
+    // not used)
+    uint32_t key[kCompactItems];
+#pragma unroll
+    for (int k = 0; k < kCompactItems; ++k) key[k] = (base + k < n) ? a.depth_key[base + k] : 0u;
     uint32_t vis = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) vis += cnt[k] > 0u;
+    for (int k = 0; k < kCompactItems; ++k) vis += cnt[k] > 0u;
     uint32_t total;
     uint32_t excl = block_excl_scan<kScanThreads>(vis, total, s_warp);
     if (threadIdx.x < 32) {
@@ -151,18 +159,15 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(CompactArgs a) {
     __syncthreads();
     uint64_t off = s_excl + excl;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      const bool vis = cnt[k] > 0u;
-      const uint32_t key = vis ? a.depth_key[base + k] : 0u;
-      if (vis) {
+    for (int k = 0; k < kCompactItems; ++k) {
+      if (cnt[k] > 0u) {
         if (off < n) {
-          a.keys_out[off] = key;
+          a.keys_out[off] = key[k];
           a.vals_out[off] = (uint32_t)(base + k);
         }
         ++off;
+        for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key[k] >> (8 * p)) & 255u)], 1u);
       }
-      if (vis)
-        for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
     }
     if (tile == num_tiles - 1 && threadIdx.x == 0) *a.n_vis_out = (uint32_t)(s_excl + total);
   }
@@ -360,14 +365,15 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(EmitArgs a) {
     const uint32_t tile = s_tile;
     if (tile >= num_tiles) break;
     const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
+    // all pair indices first, then all their tile counts (two rounds of
+    // loads in flight instead of a dependent pair per item)
     uint32_t cnt[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) cnt[k] = base + k < n_vis ? pairs[base + k] : 0xffffffffu;
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      bool valid = base + k < n_vis;
-      const uint32_t p = valid ? pairs[base + k] : 0u;
-      valid = valid && p < a.n_pairs;
-      cnt[k] = valid ? a.ntiles[p] : 0u;
+      cnt[k] = cnt[k] < a.n_pairs ? a.ntiles[cnt[k]] : 0u;
       sum += cnt[k];
     }
     uint32_t total;
