@@ -62,15 +62,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
-// q of one list entry at pixel centre (px, py).  Explicit rounding
-// intrinsics keep the forward and backward kernels bit-identical.
-__device__ __forceinline__ float entry_q(const float4& a, const float4& b, float px, float py,
-                                         float& dx, float& dy) {
-  dx = __fsub_rn(a.x, px);
-  dy = __fsub_rn(a.y, py);
-  float t1 = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));   // qa dx + qb dy
-  float t2 = __fmaf_rn(__fmul_rn(b.x, dy), dy, b.y);   // qc dy^2 + lo
-  return __fmaf_rn(t1, dx, t2);
+// q of one list entry (a, b) at the pixel centre whose negation is npix
+// = (-px, -py); d = (u - px, v - py) comes out as one packed subtraction.
+// Explicit rounding intrinsics keep the forward and backward walks
+// bit-identical.
+__device__ __forceinline__ float entry_q(const float4& a, const float4& b, float2 npix, float2& d) {
+  d = __fadd2_rn(make_float2(a.x, a.y), npix);
+  const float t1 = __fmaf_rn(a.z, d.x, __fmul_rn(a.w, d.y));   // qa dx + qb dy
+  const float t2 = __fmaf_rn(__fmul_rn(b.x, d.y), d.y, b.y);   // qc dy^2 + lo
+  return __fmaf_rn(t1, d.x, t2);
 }
 
 // Decoupled look-back status words: 2-bit flag in the top bits.

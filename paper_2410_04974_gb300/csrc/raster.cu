@@ -18,9 +18,14 @@
 // skipped when q < log2(1/255); alpha = min(0.99, 2^q); stop (excluding the
 // entry) when T (1 - alpha) < 1e-4; C += c alpha T; T *= (1 - alpha).
 // Explicit rounding intrinsics make the backward replay bit-identical.
-// The forward culls with the alpha box only (its per-entry work is too cheap
-// for the exact test to pay off); the backward, whose per-entry work is
-// several times larger, also applies the exact quadratic test.
+// The stand-alone forward culls with the alpha box only (its per-entry work
+// is too cheap for the exact test to pay off); the backward, whose
+// per-entry work is several times larger, also applies the exact quadratic
+// test, and in the fused kernel the forward applies it and records each
+// group's ballot for the backward.  Pairs of values that take the same
+// operation (the pixel offset, T (1 - alpha) and alpha T, two colour
+// channels) use the packed two-wide FP32 instructions, with the same
+// rounding as the scalar ones.
 #include <algorithm>
 
 #include "common.cuh"
@@ -92,19 +97,25 @@ __device__ __forceinline__ bool reaches(const PixelMap& m, float4 a, float4 b, f
   return best + b.y >= kQMin - 1e-3f;
 }
 
-__device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, int cnt, float4* s_a,
-                                           float4* s_b, float4* s_c) {
+// A list entry as staged in shared memory: its blend record (u, v, qa, qb),
+// (qc, lo, r, g), (b, hx, hy) and its pair index (bits of c.w).  One struct
+// per entry, so a walk addresses all three parts from one index.
+struct __align__(16) Entry {
+  float4 a, b, c;
+};
+
+__device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, int cnt, Entry* s_e) {
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     const uint32_t p = a.sorted[start + i];
     if (p < a.n_pairs) {
       const PairRec& r = a.rec[p];
-      s_a[i] = r.a;
-      s_b[i] = r.b;
-      s_c[i] = make_float4(r.c.x, r.c.y, r.c.z, __uint_as_float(p));
+      s_e[i].a = r.a;
+      s_e[i].b = r.b;
+      s_e[i].c = make_float4(r.c.x, r.c.y, r.c.z, __uint_as_float(p));
     } else {  // unreachable for a consistent sort: an entry that reaches no pixel
-      s_a[i] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
-      s_b[i] = make_float4(0.f, -1e30f, 0.f, 0.f);
-      s_c[i] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0u));
+      s_e[i].a = make_float4(-1e30f, -1e30f, 0.f, 0.f);
+      s_e[i].b = make_float4(0.f, -1e30f, 0.f, 0.f);
+      s_e[i].c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0u));
     }
   }
 }
@@ -154,26 +165,28 @@ struct FwdPixel {
 // group's ballot is recorded there for the backward walk.
 template <bool kCount>
 __device__ __forceinline__ FwdPixel fwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
-                                             uint2 range, bool inside, float4* s_a, float4* s_b, float4* s_c,
+                                             uint2 range, bool inside, Entry* s_e,
                                              uint32_t& n_eval, uint32_t& n_comp, uint32_t& n_warp,
                                              uint32_t* cull = nullptr) {
   const int B = a.batch;
   const int lane = threadIdx.x & 31;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  float T = 1.f, C2 = 0.f;
+  float2 C01 = make_float2(0.f, 0.f);
+  const float2 npix = make_float2(-pxc, -pyc);
   bool done = !inside;
   uint32_t walked = range.y - range.x;
   bool staged = false;
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
-    load_batch(a, start, cnt, s_a, s_b, s_c);
+    load_batch(a, start, cnt, s_e);
     staged = start == range.x && start + cnt == range.y;
     __syncthreads();
     if (__all_sync(0xffffffffu, done)) continue;
     for (int base = 0; base < cnt; base += 32) {
       const int jl = base + lane;
-      const bool rel = jl < cnt && (cull ? reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl])
-                                         : reaches<false>(pm, s_a[jl], s_b[jl], s_c[jl]));
+      const bool rel = jl < cnt && (cull ? reaches<true>(pm, s_e[jl].a, s_e[jl].b, s_e[jl].c)
+                                         : reaches<false>(pm, s_e[jl].a, s_e[jl].b, s_e[jl].c));
       uint32_t mask = __ballot_sync(0xffffffffu, rel);
       if (cull) {
         const uint32_t g = (start - range.x + base) >> 5;
@@ -185,19 +198,19 @@ __device__ __forceinline__ FwdPixel fwd_walk(const BlendArgs& a, const PixelMap&
         mask &= mask - 1;
         // Branch-free: a skipped (or finished) pixel takes alpha = 0, which
         // leaves T and C bit-for-bit unchanged.
-        const float4 ra = s_a[j], rb = s_b[j];
-        const float blue = s_c[j].x;
-        float dx, dy;
-        const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
+        const float4 ra = s_e[j].a, rb = s_e[j].b;
+        const float blue = s_e[j].c.x;
+        float2 d;
+        const float q = entry_q(ra, rb, npix, d);
         const bool vis = !done && q >= kQMin;
         const float alpha = vis ? fminf(kAlphaMax, ex2_approx(q)) : 0.f;
-        const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-        const bool stop = test_T < kTMin;
-        const float w = stop ? 0.f : __fmul_rn(alpha, T);
-        C0 = __fmaf_rn(rb.z, w, C0);
-        C1 = __fmaf_rn(rb.w, w, C1);
+        // (T (1 - alpha), alpha T) in one packed multiply
+        const float2 tw = __fmul2_rn(make_float2(T, T), make_float2(__fsub_rn(1.f, alpha), alpha));
+        const bool stop = tw.x < kTMin;
+        const float w = stop ? 0.f : tw.y;
+        C01 = __ffma2_rn(make_float2(rb.z, rb.w), make_float2(w, w), C01);
         C2 = __fmaf_rn(blue, w, C2);
-        T = stop ? T : test_T;
+        T = stop ? T : tw.x;
         if (stop) walked = start - range.x + j;
         if (kCount) {
           n_eval += done ? 0u : 1u;
@@ -208,16 +221,13 @@ __device__ __forceinline__ FwdPixel fwd_walk(const BlendArgs& a, const PixelMap&
       if (__all_sync(0xffffffffu, done)) break;
     }
   }
-  return FwdPixel{T, C0, C1, C2, walked, staged};
+  return FwdPixel{T, C01.x, C01.y, C2, walked, staged};
 }
 
 // Forward blend of global tile gt by the calling CTA.
 template <bool kCount, bool kStore>
 __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
-  const int B = a.batch;
-  float4* s_a = s_mem;
-  float4* s_b = s_mem + B;
-  float4* s_c = s_mem + 2 * B;
+  Entry* s_e = reinterpret_cast<Entry*>(s_mem);
   __shared__ float s_red[16];
 
   const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
@@ -229,7 +239,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendArgs& a, uint32_t gt, 
   const int lane = threadIdx.x & 31;
 
   uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
-  const FwdPixel fp = fwd_walk<kCount>(a, pm, pxc, pyc, range, inside, s_a, s_b, s_c, n_eval, n_comp, n_warp);
+  const FwdPixel fp = fwd_walk<kCount>(a, pm, pxc, pyc, range, inside, s_e, n_eval, n_comp, n_warp);
   float T = fp.T, C0 = fp.C0, C1 = fp.C1, C2 = fp.C2;
   const uint32_t walked = fp.walked;
 
@@ -285,28 +295,29 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
 }
 
 // Pass 2 over slots [0, k).  xc, yc: centre of the 8 x 4 sub-block.
-__device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws, int k, const float4* s_a,
-                                            const float4* s_c, float xc, float yc) {
+__device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws, int k, const Entry* s_e,
+                                            float xc, float yc) {
   static_assert(kSlots == kSubW && kSubH == 4, "one row of the sub-block per slot group");
   __syncwarp();
   const int lane = threadIdx.x & 31;
   const int s = lane & (kSlots - 1);
   const int r = lane >> 3;                 // row of the sub-block
   const float2* row = ws.dqw[s];
-  float R0 = 0.f, R1 = 0.f, R2 = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
+  float R1 = 0.f, R2 = 0.f;
+  float2 RG = make_float2(0.f, 0.f);    // (sum dq, sum dC2 w)
+  float2 G01 = make_float2(0.f, 0.f);   // (sum dC0 w, sum dC1 w)
 #pragma unroll
   for (int c = 0; c < kSubW; ++c) {
     const int p = r * kSubW + c;
     const float2 v = row[p ^ s];
-    const float4 dc = ws.pix[p + (p >> 3)];
+    const float4 dc = ws.pix[p + (p >> 3)];   // (dC0, dC1, 1, dC2)
     const float cc = (float)c - 0.5f * (float)(kSubW - 1);   // column about the centre
-    R0 += v.x;
     R1 = fmaf(cc, v.x, R1);
     R2 = fmaf(cc * cc, v.x, R2);
-    G0 = fmaf(dc.x, v.y, G0);
-    G1 = fmaf(dc.y, v.y, G1);
-    G2 = fmaf(dc.z, v.y, G2);
+    RG = __ffma2_rn(make_float2(dc.z, dc.w), v, RG);
+    G01 = __ffma2_rn(make_float2(dc.x, dc.y), make_float2(v.y, v.y), G01);
   }
+  const float R0 = RG.x, G0 = G01.x, G1 = G01.y, G2 = RG.y;
   const float rr = (float)r - 0.5f * (float)(kSubH - 1);      // row about the centre
   // moments of dq in (c, r) about the centre: 1, c, r, c^2, c r, r^2; then dL/dC . w
   float m[9] = {R0, R1, rr * R0, R2, rr * R1, rr * rr * R0, G0, G1, G2};
@@ -316,7 +327,7 @@ __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws,
     for (int q = 0; q < 9; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], o);
   if (lane < k) {
     const int j = ws.slot_j[lane];
-    const float U = s_a[j].x - xc, V = s_a[j].y - yc;   // dx = U - c, dy = V - r
+    const float U = s_e[j].a.x - xc, V = s_e[j].a.y - yc;   // dx = U - c, dy = V - r
     float g[9];
     g[0] = fmaf(U, m[0], -m[1]);                          // sum dq dx
     g[1] = fmaf(V, m[0], -m[2]);                          // sum dq dy
@@ -327,7 +338,7 @@ __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws,
     g[6] = m[6];
     g[7] = m[7];
     g[8] = m[8];
-    float* dst = a.grad_rec + (size_t)__float_as_uint(s_c[j].w) * 12;
+    float* dst = a.grad_rec + (size_t)__float_as_uint(s_e[j].c.w) * 12;
 #pragma unroll
     for (int q = 0; q < 9; ++q)
       if (g[q] != 0.f) red_add(dst + q, g[q]);
@@ -343,8 +354,8 @@ __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws,
 template <bool kRecompute>
 __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm, float pxc, float pyc,
                                          uint2 range, bool inside, const float* Cf, const float* dC,
-                                         uint32_t bound, bool staged, float4* s_a, float4* s_b, float4* s_c,
-                                         WarpScratch& ws, bool recorded = false) {
+                                         uint32_t bound, bool staged, Entry* s_e, WarpScratch& ws,
+                                         bool recorded = false) {
   const int B = a.batch;
   const int lane = threadIdx.x & 31;
   // dL/dalpha_i = sum_c dC_c (c_i T_i - S_c / (1 - alpha_i)) with S the colour
@@ -352,15 +363,17 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
   // sum_c dC_c S_c = D0 - Q with D0 = dC . C and Q = dC . P kept as a scalar.
   const float D0 = dC[0] * Cf[0] + dC[1] * Cf[1] + dC[2] * Cf[2];
   float T = 1.f, Q = 0.f;
+  const float2 npix = make_float2(-pxc, -pyc);
   bool done = !inside;
   if (kRecompute || !inside) bound = inside ? 0xffffffffu : 0u;   // outside the image: an empty walk
-  ws.pix[lane + (lane >> 3)] = make_float4(dC[0], dC[1], dC[2], 0.f);
+  // (dC0, dC1, 1, dC2): pass 2 pairs the 1 with dq and dC2 with w
+  ws.pix[lane + (lane >> 3)] = make_float4(dC[0], dC[1], 1.f, dC[2]);
   int k = 0;          // slots filled (warp-uniform)
 
   for (uint32_t start = range.x; start < range.y; start += B) {
     if (__syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
-    if (!staged) load_batch(a, start, cnt, s_a, s_b, s_c);
+    if (!staged) load_batch(a, start, cnt, s_e);
     __syncthreads();
     if (__all_sync(0xffffffffu, done)) continue;
     // entries j < lim of this batch lie within the pixel's walk
@@ -374,7 +387,7 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
         mask = ws.cull[g];
       } else {
         const int jl = base + lane;
-        const bool rel = jl < cnt && reaches<true>(pm, s_a[jl], s_b[jl], s_c[jl]);
+        const bool rel = jl < cnt && reaches<true>(pm, s_e[jl].a, s_e[jl].b, s_e[jl].c);
         mask = __ballot_sync(0xffffffffu, rel);
       }
       while (mask) {
@@ -383,18 +396,19 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
         // Branch-free, as in the forward: alpha = 0 for a pixel that skips
         // the entry or is finished, which leaves T and Q unchanged and gives
         // zero dq and w.
-        const float4 ra = s_a[j], rb = s_b[j];
-        const float blue = s_c[j].x;
-        float dx, dy;
-        const float q = entry_q(ra, rb, pxc, pyc, dx, dy);
+        const float4 ra = s_e[j].a, rb = s_e[j].b;
+        const float blue = s_e[j].c.x;
+        float2 d;
+        const float q = entry_q(ra, rb, npix, d);
         const bool vis = (kRecompute ? !done : j < lim) && q >= kQMin;
         const float e = ex2_approx(q);
         const float alpha = vis ? fminf(kAlphaMax, e) : 0.f;
         const float om = __fsub_rn(1.f, alpha);
-        const float test_T = __fmul_rn(T, om);
+        const float2 tw = __fmul2_rn(make_float2(T, T), make_float2(om, alpha));   // (T (1 - alpha), alpha T)
+        const float test_T = tw.x;
         // stored walk: never a stop inside it, and alpha = 0 past it
         const bool stop = kRecompute && test_T < kTMin;
-        const float w = stop ? 0.f : __fmul_rn(alpha, T);
+        const float w = stop ? 0.f : tw.y;
         const float G = dC[0] * rb.z + dC[1] * rb.w + dC[2] * blue;
         Q = fmaf(w, G, Q);   // now includes this entry: D0 - Q is behind it
         const float dLda = T * G - (D0 - Q) * __fdividef(1.f, om);
@@ -407,7 +421,7 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
         ws.dqw[k][lane ^ k] = make_float2(dq, w);
         if (lane == 0) ws.slot_j[k] = j;
         if (++k == kSlots) {
-          flush_slots(a, ws, k, s_a, s_c, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
+          flush_slots(a, ws, k, s_e, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
           k = 0;
         }
       }
@@ -415,7 +429,7 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
     }
     if (!kRecompute) done = done || start - range.x + cnt >= bound;
     if (k) {   // the slots refer to this batch's shared-memory records
-      flush_slots(a, ws, k, s_a, s_c, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
+      flush_slots(a, ws, k, s_e, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
       k = 0;
     }
   }
@@ -450,7 +464,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
     if (!kRecompute) bound = a.nwalk[cam.pixel_base + pix];
   }
   WarpScratch* ws = reinterpret_cast<WarpScratch*>(s_mem + 3 * B);
-  bwd_walk<kRecompute>(a, pm, pxc, pyc, range, inside, Cf, dC, bound, false, s_mem, s_mem + B, s_mem + 2 * B,
+  bwd_walk<kRecompute>(a, pm, pxc, pyc, range, inside, Cf, dC, bound, false, reinterpret_cast<Entry*>(s_mem),
                        ws[threadIdx.x >> 5]);
 }
 
@@ -465,9 +479,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
 // additions.
 __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt, float4* s_mem) {
   const int B = a.batch;
-  float4* s_a = s_mem;
-  float4* s_b = s_mem + B;
-  float4* s_c = s_mem + 2 * B;
+  Entry* s_e = reinterpret_cast<Entry*>(s_mem);
   __shared__ float s_red[16];
 
   const CamRec& cam = a.cams[find_camera(a.cams, a.n_cams, gt)];
@@ -481,7 +493,7 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
   WarpScratch& ws = reinterpret_cast<WarpScratch*>(s_mem + 3 * B)[threadIdx.x >> 5];
   uint32_t n_eval = 0, n_comp = 0, n_warp = 0;
   const FwdPixel fp =
-      fwd_walk<false>(a, pm, pxc, pyc, range, inside, s_a, s_b, s_c, n_eval, n_comp, n_warp, ws.cull);
+      fwd_walk<false>(a, pm, pxc, pyc, range, inside, s_e, n_eval, n_comp, n_warp, ws.cull);
   float Cf[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f};
   float l1 = 0.f;
   if (inside) {
@@ -515,7 +527,7 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
     atomicAdd(a.loss, sum * (double)a.inv_count);
   }
   __syncwarp();
-  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_a, s_b, s_c, ws, true);
+  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_e, ws, true);
 }
 
 // Register budgets of the kernels that run the backward walk (swept on the
