@@ -134,13 +134,13 @@ __device__ __forceinline__ void load_batch(const BlendArgs& a, uint32_t start, i
 //     shuffles, and lane s turns the sums into the entry's nine record
 //     gradients (moments of dq in dx = u - px, dy = v - py) and adds them to
 //     the record gradients in global memory.
-// Pass 2 reads what pass 1 stored for a slot at pixel p from index p ^ s, so
-// the row writes of pass 1 and the column reads of pass 2 are both free of
-// shared-memory bank conflicts.
+// A slot's 32 pixel values are stored with a stride of 33 (one float2 of
+// padding per slot), so the row writes of pass 1 and the column reads of
+// pass 2 are both free of shared-memory bank conflicts.
 constexpr int kSlots = 8;
 constexpr int kCullGroups = 64;   // 2,048 list entries
 struct __align__(16) WarpScratch {
-  float2 dqw[kSlots][32];   // (dL/dq / ln 2, w) of slot s at pixel p, at [s][p ^ s]
+  float2 dqw[kSlots][33];   // (dL/dq / ln 2, w) of slot s at pixel p, at [s][p]
   float4 pix[35];           // dL/dC of pixel p at p + (p >> 3) (rows in other banks)
   int slot_j[kSlots];       // batch index of the entry in slot s
   // fused kernel: the forward walk's culling ballot of list entries
@@ -309,7 +309,7 @@ __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws,
 #pragma unroll
   for (int c = 0; c < kSubW; ++c) {
     const int p = r * kSubW + c;
-    const float2 v = row[p ^ s];
+    const float2 v = row[p];
     const float4 dc = ws.pix[p + (p >> 3)];   // (dC0, dC1, 1, dC2)
     const float cc = (float)c - 0.5f * (float)(kSubW - 1);   // column about the centre
     R1 = fmaf(cc, v.x, R1);
@@ -418,7 +418,7 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
         const float dq = (!stop && e <= kAlphaMax) ? dLda * alpha : 0.f;
         T = stop ? T : test_T;
         if (kRecompute) done = done || stop;
-        ws.dqw[k][lane ^ k] = make_float2(dq, w);
+        ws.dqw[k][lane] = make_float2(dq, w);
         if (lane == 0) ws.slot_j[k] = j;
         if (++k == kSlots) {
           flush_slots(a, ws, k, s_e, 0.5f * (pm.x0 + pm.x1), 0.5f * (pm.y0 + pm.y1));
