@@ -371,10 +371,13 @@ __device__ __forceinline__ void bwd_walk(const BlendArgs& a, const PixelMap& pm,
   int k = 0;          // slots filled (warp-uniform)
 
   for (uint32_t start = range.x; start < range.y; start += B) {
-    if (__syncthreads_count(done) == (int)blockDim.x) break;
+    // a staged list is already in shared memory (read-only): no CTA barrier
+    if (!staged && __syncthreads_count(done) == (int)blockDim.x) break;
     const int cnt = (int)min((uint32_t)B, range.y - start);
-    if (!staged) load_batch(a, start, cnt, s_e);
-    __syncthreads();
+    if (!staged) {
+      load_batch(a, start, cnt, s_e);
+      __syncthreads();
+    }
     if (__all_sync(0xffffffffu, done)) continue;
     // entries j < lim of this batch lie within the pixel's walk
     const int lim = (int)min((uint32_t)cnt, bound - min(bound, start - range.x));
@@ -473,7 +476,10 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendArgs& a, uint32_t gt, 
 // 4.4): each pixel's dL/dC = sign(C - target) / M is known as soon as its
 // forward walk ends, so the backward replay follows in the same CTA with C,
 // dL/dC and the walk length in registers, and a list that fitted in one
-// batch is replayed from the shared memory the forward filled.  Images,
+// batch is replayed from the shared memory the forward filled, each warp
+// starting its backward as soon as its own forward ends (the loss partials
+// are summed after the backward, at the CTA's only barrier past the load).
+// Images,
 // dL/dC, loss and record gradients equal those of raster_fwd followed by
 // blend_bwd in stored-walk mode, bit for bit up to the order of the atomic
 // additions.
@@ -520,14 +526,14 @@ __device__ __forceinline__ void blend_fused_tile(const BlendArgs& a, uint32_t gt
   }
   l1 = warp_sum(l1);
   if (lane == 0) s_red[threadIdx.x >> 5] = l1;
+  __syncwarp();
+  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_e, ws, true);
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += s_red[w];
     atomicAdd(a.loss, sum * (double)a.inv_count);
   }
-  __syncwarp();
-  bwd_walk<false>(a, pm, pxc, pyc, range, inside, Cf, dC, fp.walked, fp.staged, s_e, ws, true);
 }
 
 // Register budgets of the kernels that run the backward walk (swept on the
