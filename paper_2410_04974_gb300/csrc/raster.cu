@@ -294,6 +294,12 @@ __device__ __forceinline__ void red_add(float* addr, float x) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(x) : "memory");
 }
 
+// Four consecutive floats (16-byte aligned) added in one vector reduction.
+__device__ __forceinline__ void red_add4(float* addr, float x, float y, float z, float w) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(x), "f"(y), "f"(z), "f"(w)
+               : "memory");
+}
+
 // Pass 2 over slots [0, k).  xc, yc: centre of the 8 x 4 sub-block.
 __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws, int k, const Entry* s_e,
                                             float xc, float yc) {
@@ -339,9 +345,10 @@ __device__ __forceinline__ void flush_slots(const BlendArgs& a, WarpScratch& ws,
     g[7] = m[7];
     g[8] = m[8];
     float* dst = a.grad_rec + (size_t)__float_as_uint(s_e[j].c.w) * 12;
-#pragma unroll
-    for (int q = 0; q < 9; ++q)
-      if (g[q] != 0.f) red_add(dst + q, g[q]);
+    // a record is 48 bytes, 16-byte aligned: floats 0-3 and 4-7 as vectors
+    red_add4(dst, g[0], g[1], g[2], g[3]);
+    red_add4(dst + 4, g[4], g[5], g[6], g[7]);
+    if (g[8] != 0.f) red_add(dst + 8, g[8]);
   }
   __syncwarp();
 }
