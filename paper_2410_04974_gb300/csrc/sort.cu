@@ -501,11 +501,8 @@ __global__ void __launch_bounds__(kScanThreads) emit_expand_kernel(EmitArgs a) {
         a.keys_out[o] = key;
         a.vals_out[o] = s_pair[lo];
       }
-      for (int q = 0; q < a.passes; ++q) {
-        const uint32_t d = key == 0xffffffffu ? 256u : (key >> (8 * q)) & 255u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[q * 256 + d], __popc(peers));
-      }
+      if (key != 0xffffffffu)
+        for (int q = 0; q < a.passes; ++q) atomicAdd(&s_hist[q * 256 + ((key >> (8 * q)) & 255u)], 1u);
     }
   }
   __syncthreads();
