@@ -244,7 +244,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(OnesweepArgs 
     for (int j = 0; j < kSortItems; ++j) {
       uint32_t idx = wbase + j * 32 + lane;
       uint32_t d = idx < n ? (key[j] >> a.shift) & 255u : 256u;
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      // lanes with the same digit, from one ballot per digit bit
+      uint32_t peers = __ballot_sync(0xffffffffu, d < 256u);
+      if (d >= 256u) peers = ~peers;
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        const uint32_t set = (d >> bit) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, set);
+        peers &= set ? bal : ~bal;
+      }
       uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
       __syncwarp();
       if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) s_whist[warp][d] = before + __popc(peers);
